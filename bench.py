@@ -1,0 +1,275 @@
+"""Benchmark of the dual-smoothing hot path (one P-APG iteration = one step).
+
+Default workload: the log-sum-exp instance with N = 20000 points in 20 dimensions
+(x ~ U[-1,1]^20, y = log sum_k exp(a_k.x) + N(0, 0.1^2), 8 terms, seed 0), FP32 multipliers
+(2 x 1.6 GB, larger than L2, so no flush is needed between steps), gamma = 1e-4.
+
+A step is one iteration: the fused Lambda sweep (every one of the N(N-1) pairs read and
+written once) plus the O(N n) finalize/recovery kernel.  ``value`` is lambda-pair updates
+per second over the timed steps (inputs already resident in HBM), timed with CUDA events on
+the library's stream; ``e2e`` is the same metric through the public API from host buffers
+(create from host X and ybar, the K iterations, and the copy of (y, xi) back to the host
+inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own instance (seed + rank, weak scaling); the
+timed region is bracketed by barriers and the slowest rank's time is reported.
+``--impl reference`` times the FP64 CPU oracle instead (on a bounded row sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import cr_synth  # noqa: E402
+
+METRIC = "lambda_pair_updates_per_s"
+UNIT = "pairs/s"
+GAMMA = 1e-4
+CPU_SAMPLE_N = 8000  # oracle sample: the first 8000 points of the same instance
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    inst = cr_synth.workload(args.workload)
+    Ns = min(CPU_SAMPLE_N, inst.N)
+    X, yb = inst.X[:Ns], inst.ybar[:Ns]
+    L = oracle.lipschitz(X, GAMMA)
+    o = oracle.PAPG(X, yb, GAMMA, L)
+    o.step(args.warmup, log=False)
+    t0 = time.perf_counter()
+    o.step(args.steps, log=False)
+    dt = time.perf_counter() - t0
+    pairs = Ns * (Ns - 1) * args.steps
+    v = pairs / dt
+    sample = (f"first {Ns} of the {inst.N} points of {args.workload}; {args.steps} oracle iterations "
+              f"(FP64 C, OpenMP)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "N": Ns, "n": inst.n, "gamma": GAMMA},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(workload):
+    import oracle
+
+    inst = cr_synth.workload(workload)
+    Ns = min(CPU_SAMPLE_N, inst.N)
+    X, yb = inst.X[:Ns], inst.ybar[:Ns]
+    o = oracle.PAPG(X, yb, GAMMA, oracle.lipschitz(X, GAMMA))
+    o.step(1, log=False)
+    iters = 6
+    t0 = time.perf_counter()
+    o.step(iters, log=False)
+    dt = time.perf_counter() - t0
+    return {"value": Ns * (Ns - 1) * iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {Ns} points of {workload}, {iters} FP64 oracle iterations ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="lse_N20000_n20")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_1608_02227_gb300 as crgb
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    prec = {"fp32": crgb.CR_FP32, "fp64": crgb.CR_FP64, "tf32": crgb.CR_MIXED_TF32}[args.precision]
+    spec = dict(cr_synth.WORKLOADS[args.workload])
+    spec["seed"] = spec.get("seed", 0) + rank
+    inst = cr_synth.make_instance(**spec)
+    N, n = inst.N, inst.n
+    pairs = N * (N - 1)
+
+    s = crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec)
+    desc = s.describe()
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    sweep_ms, total_ms = crgb.cr_dual_step_timed(s.ctx, args.steps)
+    barrier()
+    clk = clocks.stop()
+    gap = s.gap()
+    s.close()
+    t_max = total_ms
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = pairs * args.steps * ws / (t_max / 1e3)
+
+    # end to end through the public API from host buffers
+    barrier()
+    t0 = time.perf_counter()
+    with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec) as s2:
+        s2.step(args.steps)
+        y, xi = s2.primal()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": pairs * args.steps * ws / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": (inst.X.nbytes + inst.ybar.nbytes) / args.steps,
+           "d2h_bytes_per_step": (y.nbytes + xi.nbytes) / args.steps}
+
+    if rank == 0:
+        peak, src = _peaks()
+        tsz = 8 if prec == crgb.CR_FP64 else 4
+        alg_bytes = 3 * tsz * pairs  # read lambda^{k-1}, lambda^{k-2}; write lambda^k
+        sweep_avg_s = sweep_ms / 1e3 / args.steps
+        achieved = alg_bytes / sweep_avg_s / 1e9
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+        if os.path.exists(tpath):
+            with open(tpath) as fh:
+                td = json.load(fh)
+            if td.get("workload") == args.workload and td.get("precision") == args.precision:
+                traffic = td.get("bytes_per_launch")
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "n": n, "gamma": GAMMA, "precision": args.precision,
+                       "l2": "inputs larger than L2 (two N x N FP32 multiplier arrays)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "grid": desc["grid"], "rows_per_item": desc["rows_per_item"],
+                       "col_splits": desc["col_splits"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                         "kernel": "sweep", "algorithmic_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": sweep_avg_s * 1e3},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "gap_at_end": {"k": gap["k"], "rel_gap": gap["rel_gap"], "dual_g": gap["dual_g"]},
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

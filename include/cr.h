@@ -1,0 +1,156 @@
+/*
+ * cr.h -- C ABI of the GB300 (sm_103a) library for the dual smoothing method of
+ * Aybat & Wang, "A Parallelizable Dual Smoothing Method for Large Scale Convex
+ * Regression Problems" (arXiv 1608.02227).
+ *
+ * Problem (Eq. (regularize), Section 2.1): given points x_l in R^n and observations
+ * ybar_l, l = 0..N-1, find
+ *     min  1/2 ||y - ybar||^2 + gamma/2 ||xi||^2
+ *     s.t. (C eta)_ij = y_j - y_i + xi_i . (x_i - x_j) >= 0   for all i != j
+ * (Eq. (original): the first-order convexity conditions of a fitted convex function
+ * with values y_l and subgradients xi_l).  Every one of the N(N-1) constraints is
+ * dualised (the K = N case of the partition of Section 2.1), so the multipliers form
+ * an N x N matrix Lambda (lambda_ij of pair (i, j), diagonal unused) and Step 1 of
+ * P-APG (Figure "papg") is the closed form
+ *     y = ybar + a,  xi = b / gamma,  (a, b) = C^T lambda,
+ *     a_l = sum_i lambda_il - sum_j lambda_lj,   b_l = sum_j lambda_lj (x_l - x_j).
+ * One iteration k is then (Steps 2-4 of Figure "papg", Eq. (dual gradient)):
+ *     lambda~ = lambda^{k-1} + beta_k (lambda^{k-1} - lambda^{k-2}),
+ *     rho_ij  = -(C eta(lambda~))_ij = y_i - y_j + xi_i . (x_j - x_i),
+ *     lambda^k_ij = max(0, lambda~_ij + rho_ij / L),
+ *     t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  beta_{k+1} = (t_k - 1) / t_{k+1},
+ * with L an upper bound on the Lipschitz constant of grad g_gamma (Eq. (lischitz)).
+ *
+ * Conventions of every entry point:
+ *   - Pointers may be host or device memory of the context's device (copies use
+ *     unified addressing, cudaMemcpyDefault).  Arrays are dense and row-major: X is N x n
+ *     (X[l*n + k]), xi is N x n, Lambda is N x N with leading dimension ld.
+ *   - The library copies its inputs; the caller owns every buffer it passes.
+ *   - Errors are returned as cr_status; nothing throws across the ABI.  The text
+ *     of the last failure on the calling thread is returned by cr_last_error().
+ *   - A context is bound to the CUDA device that was current at cr_create and to
+ *     one stream; it is not thread-safe (one thread at a time per context).
+ */
+#ifndef CR_H
+#define CR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CR_API __attribute__((visibility("default")))
+
+typedef struct cr_ctx cr_ctx;
+
+typedef enum {
+    CR_OK = 0,
+    CR_EINVAL = 1,       /* bad argument: N < 2, n < 1, n > CR_MAX_N, gamma <= 0, non-finite data */
+    CR_ENOMEM = 2,       /* a device or host allocation failed */
+    CR_ECUDA = 3,        /* a CUDA call failed (message in cr_last_error) */
+    CR_ENOTCONV = 4,     /* cr_solve reached max_iter before rel_gap_tol */
+    CR_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+    CR_ENUMERIC = 6,     /* a non-finite objective or gap was produced */
+    CR_EUNSUPPORTED = 7  /* the requested mode is not available on this device */
+} cr_status;
+
+typedef enum {
+    CR_FP64 = 0,         /* Lambda, residuals and reductions in FP64 (parity mode) */
+    CR_FP32 = 1,         /* Lambda FP32 in HBM, FP32 residuals with hi+lo y and u, FP64 recovery */
+    CR_MIXED_TF32 = 2    /* Lambda FP32, xi.x and Lambda.X on tcgen05 (TF32, hi+lo split) */
+} cr_precision;
+
+typedef enum {
+    CR_L_HESSIAN = 0,    /* L = 2N + sigma_max(A2)^2 / gamma >= lambda_max(C G^-1 C^T) */
+    CR_L_PAPER = 1       /* L = (2N + sigma_max(A2)^2) / gamma >= sigma_max(C)^2 / gamma, Eq. (lischitz) */
+} cr_lipschitz_rule;
+
+#define CR_MAX_N 32      /* largest point dimension n supported by the kernels */
+
+typedef struct cr_options {
+    double gamma;        /* Tikhonov parameter gamma > 0 (Section 5 uses 1e-4) */
+    double lipschitz;    /* 0: computed on the device at cr_create; > 0: used as L */
+    int lipschitz_rule;  /* cr_lipschitz_rule, used when lipschitz == 0 */
+    int precision;       /* cr_precision */
+    int accelerate;      /* 1: P-APG momentum (Step 4); 0: projected dual gradient ascent */
+    int check_every;     /* iterations between convergence checks in cr_solve (>= 1) */
+    int graph_iters;     /* iterations per captured CUDA graph in cr_dual_step (even; 0: no graphs) */
+    int tile_cols;       /* columns of Lambda per work item (multiple of 128; 0: chosen by the library) */
+    int deterministic;   /* kept for ABI stability: every reduction is already in a fixed order */
+} cr_options;
+
+/* Convergence record for eta(lambda^k), the primal of Theorem "rate". */
+typedef struct cr_gap_info {
+    long long k;         /* iterations taken */
+    double dual_g;       /* g_gamma(lambda^k) = -1/2||a||^2 - a.ybar - ||b||^2/(2 gamma) */
+    double primal_r;     /* r_gamma(eta(lambda^k)) = 1/2||a||^2 + ||b||^2/(2 gamma) */
+    double lagr_gap;     /* <lambda^k, C eta(lambda^k)> = primal_r - dual_g (Section 5.1 duality gap) */
+    double infeas_norm;  /* ||(C eta(lambda^k))_-||_2 / sqrt(N^2 - N) (Section 5.1 infeasibility) */
+    double rel_gap;      /* max(|lagr_gap| / primal_r, infeas_norm / rms(ybar)) */
+    double cert_primal;  /* r_gamma of the feasible max-affine repair of eta(lambda^k): >= p*_gamma */
+    double cert_gap_rel; /* (cert_primal - dual_g) / cert_primal: a certified bound on (p* - g)/p* */
+} cr_gap_info;
+
+/* Fills *opt with the defaults: gamma 1e-4, lipschitz 0 (computed), CR_L_HESSIAN,
+ * CR_FP32, accelerate 1, check_every 100, graph_iters 32, tile_cols 0. */
+CR_API void cr_default_options(cr_options *opt);
+
+/* Creates a solver for one instance (Eq. (regularize)).
+ *   X: N x n points (host or device, FP64); ybar: N observations (FP64);
+ *   opt: NULL for the defaults; stream: a cudaStream_t other than the legacy default
+ *   stream, or NULL (or the legacy stream) for a stream the context creates and owns.  Copies X and ybar to the device, computes L (Section
+ *   3's "Preprocess", on the device) unless opt->lipschitz > 0, allocates the two
+ *   N x N multiplier buffers and sets lambda^0 = 0 (theta^0 = 0, t_1 = 1).
+ *   Errors: CR_EINVAL (N < 2, n < 1 or > CR_MAX_N, gamma <= 0, non-finite inputs),
+ *   CR_ENOMEM, CR_ECUDA.  On error *out is NULL. */
+CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int n,
+                           const cr_options *opt, void *stream, cr_ctx **out);
+
+/* Enqueues `iters` P-APG iterations (Figure "papg", K = N) on the context's stream and
+ * returns without waiting.  Each iteration is the fused Lambda sweep (Steps 2 and 4 and
+ * the reductions of C^T) followed by the recovery of Step 1 for the next iteration. */
+CR_API cr_status cr_dual_step(cr_ctx *ctx, int iters);
+
+/* Runs iterations until rel_gap <= rel_gap_tol (CR_OK) or max_iter iterations in total
+ * have been taken (CR_ENOTCONV); checks every opt->check_every iterations.  *out (may
+ * be NULL) receives the last record.  Blocks the calling thread. */
+CR_API cr_status cr_solve(cr_ctx *ctx, double rel_gap_tol, long long max_iter, cr_gap_info *out);
+
+/* Copies eta(lambda^k) = (y, xi) (FP64; y: N, xi: N x n) into caller buffers (host or
+ * device).  Synchronises the stream. */
+CR_API cr_status cr_primal(const cr_ctx *ctx, double *y, double *xi);
+
+/* Computes the convergence record at the current iterate, including the pass over all
+ * pairs that gives infeas_norm and the certified repair (cert_primal).  Synchronises. */
+CR_API cr_status cr_gap(cr_ctx *ctx, cr_gap_info *out);
+
+/* Copies rows [row0, row0 + rows) of lambda^k as FP64 into out (rows x N, leading
+ * dimension ld >= N; host or device).  Synchronises.  For parity checks and checkpoints. */
+CR_API cr_status cr_lambda(const cr_ctx *ctx, long long row0, long long rows, double *out,
+                           long long ld);
+
+/* Enqueues `iters` iterations like cr_dual_step, without graphs, with CUDA events around
+ * every launch of the Lambda sweep; returns after the stream drains with *sweep_ms = the
+ * summed device time of the sweeps and *total_ms = the device time of all iterations. */
+CR_API cr_status cr_dual_step_timed(cr_ctx *ctx, int iters, float *sweep_ms, float *total_ms);
+
+/* Writes a one-line JSON description of the context (sizes, tile shape, grid, bytes per
+ * iteration, L) into buf (always NUL-terminated). */
+CR_API cr_status cr_describe(const cr_ctx *ctx, char *buf, int len);
+
+/* Returns the step constant L in use. */
+CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
+
+/* Iterations taken so far. */
+CR_API long long cr_iterations(const cr_ctx *ctx);
+
+/* Releases every resource of the context (NULL is ignored). */
+CR_API void cr_destroy(cr_ctx *ctx);
+
+CR_API const char *cr_strerror(cr_status s);
+CR_API const char *cr_last_error(void);
+CR_API int cr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CR_H */

@@ -1,0 +1,217 @@
+"""GB300 (sm_103a) library for the dual smoothing method of Aybat & Wang (arXiv 1608.02227).
+
+Python binding of the C ABI in include/cr.h.  Every function here only marshals
+arguments; every step of the method runs in the CUDA kernels of ``csrc/``.  Inputs may
+be numpy arrays (host) or torch tensors (host or CUDA); outputs are numpy arrays unless
+``device=True`` (torch CUDA tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (CR_FP32, CR_FP64, CR_L_HESSIAN, CR_L_PAPER, CR_MAX_N, CR_MIXED_TF32, CRError,
+                    cr_gap_info, cr_options, check)
+
+__all__ = [
+    "CR_FP64", "CR_FP32", "CR_MIXED_TF32", "CR_L_HESSIAN", "CR_L_PAPER", "CR_MAX_N", "CRError",
+    "default_options", "cr_create", "cr_dual_step", "cr_dual_step_timed", "cr_solve", "cr_primal",
+    "cr_gap", "cr_lambda", "cr_lipschitz", "cr_iterations", "cr_describe", "cr_destroy", "Solver",
+    "library_path",
+]
+
+
+def library_path() -> str:
+    return _capi.LIB_PATH
+
+
+def _lib():
+    return _capi.load()
+
+
+def default_options(**kw) -> cr_options:
+    o = cr_options()
+    _lib().cr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """Data pointer of a C-contiguous float64 numpy array or torch tensor (host or CUDA)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise TypeError("tensors must be contiguous float64")
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream) if stream else None
+    h = getattr(stream, "cuda_stream", None)
+    if h is None:
+        raise TypeError("stream must be a torch.cuda.Stream, an int handle or None")
+    return ctypes.c_void_p(h) if h else None
+
+
+def cr_create(X, ybar, opt: cr_options | None = None, stream=None):
+    """Create a context for one instance; returns an opaque handle (ctypes.c_void_p)."""
+    xp, xk = _ptr(X)
+    yp, yk = _ptr(ybar)
+    shape = tuple(getattr(xk, "shape", ()))
+    if len(shape) != 2:
+        raise ValueError("X must be 2-d (N x n)")
+    N, n = int(shape[0]), int(shape[1])
+    if int(np.prod(getattr(yk, "shape", (0,)))) != N:
+        raise ValueError("ybar must have N entries")
+    out = ctypes.c_void_p()
+    st = _lib().cr_create(xp, yp, N, n, ctypes.byref(opt) if opt is not None else None,
+                          _stream_handle(stream), ctypes.byref(out))
+    check(st)
+    return out
+
+
+def cr_dual_step(ctx, iters: int):
+    check(_lib().cr_dual_step(ctx, int(iters)))
+
+
+def cr_dual_step_timed(ctx, iters: int):
+    sw = ctypes.c_float()
+    tot = ctypes.c_float()
+    check(_lib().cr_dual_step_timed(ctx, int(iters), ctypes.byref(sw), ctypes.byref(tot)))
+    return float(sw.value), float(tot.value)
+
+
+def cr_solve(ctx, rel_gap_tol: float, max_iter: int):
+    """Returns (converged: bool, record dict)."""
+    g = cr_gap_info()
+    st = _lib().cr_solve(ctx, float(rel_gap_tol), int(max_iter), ctypes.byref(g))
+    if st not in (_capi.CR_OK, _capi.CR_ENOTCONV):
+        check(st)
+    return st == _capi.CR_OK, g.as_dict()
+
+
+def cr_gap(ctx):
+    g = cr_gap_info()
+    check(_lib().cr_gap(ctx, ctypes.byref(g)))
+    return g.as_dict()
+
+
+def _shape_of(ctx):
+    import json
+    d = json.loads(cr_describe(ctx))
+    return d["N"], d["n"]
+
+
+def cr_primal(ctx, device: bool = False):
+    """eta(lambda^k) = (y, xi) as float64 arrays (numpy, or torch CUDA tensors)."""
+    N, n = _shape_of(ctx)
+    if device:
+        import torch
+        y = torch.empty(N, dtype=torch.float64, device="cuda")
+        xi = torch.empty((N, n), dtype=torch.float64, device="cuda")
+        check(_lib().cr_primal(ctx, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(xi.data_ptr())))
+        return y, xi
+    y = np.empty(N)
+    xi = np.empty((N, n))
+    check(_lib().cr_primal(ctx, ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(xi.ctypes.data)))
+    return y, xi
+
+
+def cr_lambda(ctx, row0: int = 0, rows: int | None = None, device: bool = False):
+    """Rows [row0, row0+rows) of lambda^k as float64 (numpy, or a torch CUDA tensor)."""
+    N, _ = _shape_of(ctx)
+    rows = N - row0 if rows is None else rows
+    if device:
+        import torch
+        out = torch.empty((rows, N), dtype=torch.float64, device="cuda")
+        check(_lib().cr_lambda(ctx, row0, rows, ctypes.c_void_p(out.data_ptr()), N))
+        return out
+    out = np.empty((rows, N))
+    check(_lib().cr_lambda(ctx, row0, rows, ctypes.c_void_p(out.ctypes.data), N))
+    return out
+
+
+def cr_lipschitz(ctx) -> float:
+    v = ctypes.c_double()
+    check(_lib().cr_lipschitz(ctx, ctypes.byref(v)))
+    return float(v.value)
+
+
+def cr_iterations(ctx) -> int:
+    return int(_lib().cr_iterations(ctx))
+
+
+def cr_describe(ctx) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    check(_lib().cr_describe(ctx, buf, len(buf)))
+    return buf.value.decode()
+
+
+def cr_destroy(ctx):
+    if ctx:
+        _lib().cr_destroy(ctx)
+
+
+class Solver:
+    """Owning wrapper of one context (closes it on ``close()``/``with``)."""
+
+    def __init__(self, X, ybar, stream=None, **options):
+        self.opt = default_options(**options)
+        self.ctx = cr_create(X, ybar, self.opt, stream)
+
+    def step(self, iters=1):
+        cr_dual_step(self.ctx, iters)
+
+    def solve(self, tol, max_iter):
+        return cr_solve(self.ctx, tol, max_iter)
+
+    def gap(self):
+        return cr_gap(self.ctx)
+
+    def primal(self, device=False):
+        return cr_primal(self.ctx, device)
+
+    def lam(self, row0=0, rows=None, device=False):
+        return cr_lambda(self.ctx, row0, rows, device)
+
+    @property
+    def L(self):
+        return cr_lipschitz(self.ctx)
+
+    @property
+    def k(self):
+        return cr_iterations(self.ctx)
+
+    def describe(self):
+        import json
+        return json.loads(cr_describe(self.ctx))
+
+    def close(self):
+        if self.ctx:
+            cr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,779 @@
+// cr_api.cu -- host side of the C ABI declared in include/cr.h: context set-up, the
+// per-iteration launch sequence (sweep -> finalize/recovery), CUDA-graph replay of
+// iteration blocks, the solve loop and the result copies.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "cr_internal.cuh"
+
+using namespace cr;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+#define CR_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;                 \
+        }                                                                                  \
+    } while (0)
+
+}  // namespace
+
+struct cr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int N = 0, n = 0, NP = 0;
+    long long ld = 0, ldv = 0;
+    cr_options opt{};
+    double L = 0.0, a2s2 = 0.0, ybar_rms = 1.0;
+    long long k = 0;  // iterations enqueued
+    int sms = 0;
+
+    std::vector<void *> allocs;
+    double *X = nullptr, *ybar = nullptr;
+    float *xT32 = nullptr;
+    double *xT64 = nullptr;
+    void *lam[2] = {nullptr, nullptr};
+    double *ha[2] = {nullptr, nullptr}, *hb[2] = {nullptr, nullptr};
+    float *yh = nullptr, *yl = nullptr, *uh = nullptr, *ul = nullptr, *xiT = nullptr;
+    double *y64 = nullptr, *u64 = nullptr, *xiT64 = nullptr;
+    void *rowpart = nullptr, *colpart = nullptr;
+    double *finblk = nullptr, *certblk = nullptr, *log = nullptr;
+    DevState *st = nullptr;
+    // certificate buffers
+    float *c_yh = nullptr, *c_yl = nullptr, *c_uh = nullptr, *c_ul = nullptr, *c_xiT = nullptr;
+    double *c_y64 = nullptr, *c_u64 = nullptr, *c_xiT64 = nullptr;
+    double *pmax = nullptr, *pinf = nullptr;
+    int *parg = nullptr;
+    int cert_R = 1;
+    // primal scratch
+    double *tmp_y = nullptr, *tmp_xi = nullptr;
+    int *flag = nullptr;
+    // sweep shape
+    int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
+    // graph of graph_iters iterations starting at an even k
+    cudaGraphExec_t gexec = nullptr;
+    int glen = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+template <typename T>
+cr_status dev_alloc(cr_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_err("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
+    }
+    c->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return CR_OK;
+}
+
+#define CR_TRY(x)                       \
+    do {                                \
+        cr_status s_ = (x);             \
+        if (s_ != CR_OK) return s_;     \
+    } while (0)
+
+bool is_f64(const cr_ctx *c) { return c->opt.precision == CR_FP64; }
+
+// Column splits: enough work items for every SM to get several, with the tail wave as
+// full as possible; a split is a whole number of 128-column chunks.
+void choose_split(cr_ctx *c) {
+    const long long chunks = (c->ld + kChunk - 1) / kChunk;
+    const int G = std::max(1, c->sms * std::max(1, c->occ));
+    if (c->opt.tile_cols > 0) {
+        c->cps = (int)round_up(c->opt.tile_cols, kChunk);
+        c->S = (int)((c->ld + c->cps - 1) / c->cps);
+    } else {
+        int bestS = 1;
+        double bestCost = 1e300;
+        const int Smax = (int)std::min<long long>(chunks, 64);
+        for (int S = 1; S <= Smax; ++S) {
+            const long long cps_chunks = (chunks + S - 1) / S;
+            const int Sreal = (int)((chunks + cps_chunks - 1) / cps_chunks);
+            const long long items = (long long)c->RB * Sreal;
+            const long long waves = (items + G - 1) / G;
+            // time ~ waves x item length (+ a per-item start cost of ~2 chunks)
+            const double cost = (double)waves * (double)(cps_chunks + 2);
+            if (cost < bestCost * 0.999) {
+                bestCost = cost;
+                bestS = S;
+            }
+        }
+        const long long cps_chunks = (chunks + bestS - 1) / bestS;
+        c->cps = (int)(cps_chunks * kChunk);
+        c->S = (int)((chunks + cps_chunks - 1) / cps_chunks);
+    }
+    const long long items = (long long)c->RB * c->S;
+    c->grid = (int)std::min<long long>(items, (long long)G);
+}
+
+cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */, cudaEvent_t e0,
+                            cudaEvent_t e1) {
+    const int P = (int)((k - 1) & 1), Q = (int)(k & 1);
+    if (e0) CR_CUDA(cudaEventRecord(e0, c->stream));
+    if (is_f64(c)) {
+        SweepArgsD a{};
+        a.P = (const double *)c->lam[P];
+        a.Q = (double *)c->lam[Q];
+        a.ld = c->ld;
+        a.N = c->N;
+        a.row_blocks = c->RB;
+        a.col_splits = c->S;
+        a.cols_per_split = c->cps;
+        a.ldv = c->ldv;
+        a.xT = c->xT64;
+        a.y = c->y64;
+        a.u = c->u64;
+        a.xiT = c->xiT64;
+        a.st = c->st;
+        a.rowpart = (double *)c->rowpart;
+        a.colpart = (double *)c->colpart;
+        CR_CUDA(launch_sweep_d(c->NP, a, c->grid, c->stream));
+    } else {
+        SweepArgsF a{};
+        a.P = (const float *)c->lam[P];
+        a.Q = (float *)c->lam[Q];
+        a.ld = c->ld;
+        a.N = c->N;
+        a.row_blocks = c->RB;
+        a.col_splits = c->S;
+        a.cols_per_split = c->cps;
+        a.ldv = c->ldv;
+        a.xT = c->xT32;
+        a.yh = c->yh;
+        a.yl = c->yl;
+        a.uh = c->uh;
+        a.ul = c->ul;
+        a.xiT = c->xiT;
+        a.st = c->st;
+        a.rowpart = (float *)c->rowpart;
+        a.colpart = (float *)c->colpart;
+        CR_CUDA(launch_sweep_f(c->NP, a, c->grid, c->stream));
+    }
+    if (e1) CR_CUDA(cudaEventRecord(e1, c->stream));
+    FinArgs f{};
+    f.N = c->N;
+    f.n = c->n;
+    f.NP = c->NP;
+    f.precision = c->opt.precision;
+    f.col_splits = c->S;
+    f.row_blocks = c->RB;
+    f.ld = c->ld;
+    f.ldv = c->ldv;
+    f.rowpart = c->rowpart;
+    f.colpart = c->colpart;
+    f.X = c->X;
+    f.ybar = c->ybar;
+    f.a_new = c->ha[k & 1];
+    f.b_new = c->hb[k & 1];
+    f.a_old = c->ha[(k - 1) & 1];
+    f.b_old = c->hb[(k - 1) & 1];
+    f.yh = c->yh;
+    f.yl = c->yl;
+    f.uh = c->uh;
+    f.ul = c->ul;
+    f.xiT = c->xiT;
+    f.y64 = c->y64;
+    f.u64 = c->u64;
+    f.xiT64 = c->xiT64;
+    f.xT32 = c->xT32;
+    f.blockpart = c->finblk;
+    f.log = c->log;
+    f.st = c->st;
+    f.init = 0;
+    CR_CUDA(launch_finalize(f, c->stream));
+    return CR_OK;
+}
+
+cr_status build_graph(cr_ctx *c) {
+    if (c->gexec) return CR_OK;
+    const int len = c->opt.graph_iters;
+    cudaGraph_t g = nullptr;
+    CR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cr_status s = CR_OK;
+    for (int i = 0; i < len && s == CR_OK; ++i) s = enqueue_iteration(c, 2 + i /* even start */, nullptr, nullptr);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != CR_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        set_err("graph capture failed: %s", cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        set_err("graph instantiation failed: %s", cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
+    c->glen = len;
+    return CR_OK;
+}
+
+cr_status fetch_state(const cr_ctx *c, DevState *h) {
+    CR_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
+
+cr_status check_finite_host(cr_ctx *c, const double *dev, long long count, const char *what) {
+    CR_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CR_CUDA(launch_check_finite(dev, count, c->flag, c->stream));
+    int h = 0;
+    CR_CUDA(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) {
+        set_err("%s contains a non-finite value", what);
+        return CR_EINVAL;
+    }
+    return CR_OK;
+}
+
+cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
+    const int N = c->N, n = c->n;
+    CR_CUDA(cudaGetDevice(&c->device));
+    CR_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->NP = bucket_np(n);
+    c->ld = round_up(N, 32);
+    c->ldv = round_up(N, kChunk);
+    const bool f64 = is_f64(c);
+    const size_t tsz = f64 ? sizeof(double) : sizeof(float);
+
+    SweepConfig cfg{};
+    if (!(f64 ? sweep_config_d(c->NP, &cfg) : sweep_config_f(c->NP, &cfg))) {
+        set_err("no sweep kernel for n = %d", n);
+        return CR_EINVAL;
+    }
+    c->rows = cfg.rows;
+    c->RB = (N + c->rows - 1) / c->rows;
+    CR_CUDA(f64 ? sweep_occupancy_d(c->NP, &c->occ) : sweep_occupancy_f(c->NP, &c->occ));
+    if (c->occ < 1) c->occ = 1;
+    choose_split(c);
+
+    CR_TRY(dev_alloc(c, &c->X, (size_t)N * n));
+    CR_TRY(dev_alloc(c, &c->ybar, (size_t)N));
+    CR_TRY(dev_alloc(c, &c->flag, 1));
+    CR_CUDA(cudaMemcpyAsync(c->X, X, sizeof(double) * N * n, cudaMemcpyDefault, c->stream));
+    CR_CUDA(cudaMemcpyAsync(c->ybar, ybar, sizeof(double) * N, cudaMemcpyDefault, c->stream));
+    CR_TRY(check_finite_host(c, c->X, (long long)N * n, "X"));
+    CR_TRY(check_finite_host(c, c->ybar, N, "ybar"));
+    {
+        std::vector<double> hy(N);
+        CR_CUDA(cudaMemcpy(hy.data(), c->ybar, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        double s = 0.0;
+        for (double v : hy) s += v * v;
+        c->ybar_rms = sqrt(s / N);
+        if (!(c->ybar_rms > 0.0)) c->ybar_rms = 1.0;
+    }
+
+    const size_t vec = (size_t)c->ldv;
+    const size_t tvec = (size_t)c->NP * c->ldv;
+    if (f64) {
+        CR_TRY(dev_alloc(c, &c->xT64, tvec));
+        CR_TRY(dev_alloc(c, &c->y64, vec));
+        CR_TRY(dev_alloc(c, &c->u64, vec));
+        CR_TRY(dev_alloc(c, &c->xiT64, tvec));
+        CR_TRY(dev_alloc(c, &c->c_y64, vec));
+        CR_TRY(dev_alloc(c, &c->c_u64, vec));
+        CR_TRY(dev_alloc(c, &c->c_xiT64, tvec));
+        CR_CUDA(cudaMemsetAsync(c->xiT64, 0, tvec * sizeof(double), c->stream));
+        CR_CUDA(cudaMemsetAsync(c->c_xiT64, 0, tvec * sizeof(double), c->stream));
+        CR_CUDA(cudaMemsetAsync(c->y64, 0, vec * sizeof(double), c->stream));
+        CR_CUDA(cudaMemsetAsync(c->u64, 0, vec * sizeof(double), c->stream));
+    } else {
+        CR_TRY(dev_alloc(c, &c->xT32, tvec));
+        float **f[] = {&c->yh, &c->yl, &c->uh, &c->ul, &c->c_yh, &c->c_yl, &c->c_uh, &c->c_ul};
+        for (float **p : f) {
+            CR_TRY(dev_alloc(c, p, vec));
+            CR_CUDA(cudaMemsetAsync(*p, 0, vec * sizeof(float), c->stream));
+        }
+        CR_TRY(dev_alloc(c, &c->xiT, tvec));
+        CR_TRY(dev_alloc(c, &c->c_xiT, tvec));
+        CR_CUDA(cudaMemsetAsync(c->xiT, 0, tvec * sizeof(float), c->stream));
+        CR_CUDA(cudaMemsetAsync(c->c_xiT, 0, tvec * sizeof(float), c->stream));
+    }
+    CR_CUDA(launch_transpose_points(c->X, N, n, c->NP, c->ldv, c->xT32, c->xT64, c->stream));
+
+    // step constant (Section 3 "Preprocess" + Eq. (lischitz))
+    if (c->opt.lipschitz > 0.0) {
+        c->L = c->opt.lipschitz;
+    } else {
+        CR_CUDA(a2_sigma_sq(c->X, N, n, &c->a2s2, c->stream));
+        c->L = (c->opt.lipschitz_rule == CR_L_PAPER) ? (2.0 * N + c->a2s2) / c->opt.gamma
+                                                     : 2.0 * N + c->a2s2 / c->opt.gamma;
+    }
+    if (!(c->L > 0.0) || !isfinite(c->L)) {
+        set_err("invalid Lipschitz constant %g", c->L);
+        return CR_ENUMERIC;
+    }
+
+    // multipliers: lambda^0 = lambda^{-1} = 0
+    const size_t lam_count = (size_t)N * c->ld;
+    for (int i = 0; i < 2; ++i) {
+        if (f64) {
+            double *p;
+            CR_TRY(dev_alloc(c, &p, lam_count));
+            c->lam[i] = p;
+        } else {
+            float *p;
+            CR_TRY(dev_alloc(c, &p, lam_count));
+            c->lam[i] = p;
+        }
+        CR_CUDA(cudaMemsetAsync(c->lam[i], 0, lam_count * tsz, c->stream));
+        CR_TRY(dev_alloc(c, &c->ha[i], (size_t)N));
+        CR_TRY(dev_alloc(c, &c->hb[i], (size_t)N * n));
+        CR_CUDA(cudaMemsetAsync(c->ha[i], 0, sizeof(double) * N, c->stream));
+        CR_CUDA(cudaMemsetAsync(c->hb[i], 0, sizeof(double) * N * n, c->stream));
+    }
+    const size_t rp = (size_t)c->S * N * (c->NP + 1), cp = (size_t)c->RB * c->ld;
+    if (f64) {
+        double *a, *b;
+        CR_TRY(dev_alloc(c, &a, rp));
+        CR_TRY(dev_alloc(c, &b, cp));
+        c->rowpart = a;
+        c->colpart = b;
+    } else {
+        float *a, *b;
+        CR_TRY(dev_alloc(c, &a, rp));
+        CR_TRY(dev_alloc(c, &b, cp));
+        c->rowpart = a;
+        c->colpart = b;
+    }
+    const int gN = (N + 255) / 256;
+    CR_TRY(dev_alloc(c, &c->finblk, (size_t)gN * 3));
+    CR_TRY(dev_alloc(c, &c->certblk, (size_t)gN * 2));
+    CR_TRY(dev_alloc(c, &c->log, (size_t)kLogCap * 3));
+    CR_TRY(dev_alloc(c, &c->st, 1));
+    CR_TRY(dev_alloc(c, &c->tmp_y, (size_t)N));
+    CR_TRY(dev_alloc(c, &c->tmp_xi, (size_t)N * n));
+    // certificate row splits: fill about two waves of the GPU
+    c->cert_R = std::max(1, std::min(64, (2 * c->sms + gN - 1) / gN));
+    while (c->cert_R > 1 && (N + c->cert_R - 1) / c->cert_R < 64) --c->cert_R;
+    CR_TRY(dev_alloc(c, &c->pmax, (size_t)c->cert_R * N));
+    CR_TRY(dev_alloc(c, &c->pinf, (size_t)c->cert_R * N));
+    CR_TRY(dev_alloc(c, &c->parg, (size_t)c->cert_R * N));
+
+    DevState h{};
+    h.t = 1.0;
+    h.beta = 0.0;
+    h.s = 1.0 / c->L;
+    h.gamma = c->opt.gamma;
+    h.k = 0;
+    h.accelerate = c->opt.accelerate ? 1 : 0;
+    CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+
+    // eta(lambda~^1) = eta(lambda^0) = (ybar, 0)
+    FinArgs f{};
+    f.N = N;
+    f.n = n;
+    f.NP = c->NP;
+    f.precision = c->opt.precision;
+    f.col_splits = c->S;
+    f.row_blocks = c->RB;
+    f.ld = c->ld;
+    f.ldv = c->ldv;
+    f.X = c->X;
+    f.ybar = c->ybar;
+    f.a_new = c->ha[0];
+    f.b_new = c->hb[0];
+    f.a_old = c->ha[1];
+    f.b_old = c->hb[1];
+    f.yh = c->yh;
+    f.yl = c->yl;
+    f.uh = c->uh;
+    f.ul = c->ul;
+    f.xiT = c->xiT;
+    f.y64 = c->y64;
+    f.u64 = c->u64;
+    f.xiT64 = c->xiT64;
+    f.xT32 = c->xT32;
+    f.blockpart = c->finblk;
+    f.log = c->log;
+    f.st = c->st;
+    f.init = 1;
+    CR_CUDA(launch_finalize(f, c->stream));
+    CR_CUDA(cudaEventCreate(&c->ev[0]));
+    CR_CUDA(cudaEventCreate(&c->ev[1]));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+CR_API void cr_default_options(cr_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->gamma = 1e-4;
+    o->lipschitz = 0.0;
+    o->lipschitz_rule = CR_L_HESSIAN;
+    o->precision = CR_FP32;
+    o->accelerate = 1;
+    o->check_every = 100;
+    o->graph_iters = 32;
+    o->tile_cols = 0;
+    o->deterministic = 1;
+}
+
+CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int n, const cr_options *opt,
+                           void *stream, cr_ctx **out) {
+    if (!out) {
+        set_err("out is NULL");
+        return CR_EINVAL;
+    }
+    *out = nullptr;
+    cr_options o;
+    if (opt)
+        o = *opt;
+    else
+        cr_default_options(&o);
+    if (!X || !ybar) {
+        set_err("X or ybar is NULL");
+        return CR_EINVAL;
+    }
+    if (N < 2 || N > (1LL << 30)) {
+        set_err("N = %lld out of range [2, 2^30]", N);
+        return CR_EINVAL;
+    }
+    if (n < 1 || n > CR_MAX_N) {
+        set_err("n = %d out of range [1, %d]", n, CR_MAX_N);
+        return CR_EINVAL;
+    }
+    if (!(o.gamma > 0.0) || !isfinite(o.gamma)) {
+        set_err("gamma must be finite and > 0");
+        return CR_EINVAL;
+    }
+    if (o.precision != CR_FP64 && o.precision != CR_FP32 && o.precision != CR_MIXED_TF32) {
+        set_err("unknown precision %d", o.precision);
+        return CR_EINVAL;
+    }
+    if (o.precision == CR_MIXED_TF32) {
+        set_err("CR_MIXED_TF32 is not built into this library");
+        return CR_EUNSUPPORTED;
+    }
+    if (!(o.lipschitz >= 0.0) || !isfinite(o.lipschitz)) {
+        set_err("lipschitz must be finite and >= 0");
+        return CR_EINVAL;
+    }
+    if (o.check_every < 1) o.check_every = 1;
+    if (o.graph_iters < 0 || (o.graph_iters & 1)) {
+        set_err("graph_iters must be even and >= 0");
+        return CR_EINVAL;
+    }
+    if (o.tile_cols < 0) {
+        set_err("tile_cols must be >= 0");
+        return CR_EINVAL;
+    }
+    cr_ctx *c = new (std::nothrow) cr_ctx();
+    if (!c) {
+        set_err("host allocation failed");
+        return CR_ENOMEM;
+    }
+    c->N = (int)N;
+    c->n = n;
+    c->opt = o;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            set_err("cudaStreamCreate failed: %s", cudaGetErrorString(e));
+            delete c;
+            return CR_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    cr_status s = create_impl(c, X, ybar);
+    if (s != CR_OK) {
+        cr_destroy(c);
+        return s;
+    }
+    *out = c;
+    return CR_OK;
+}
+
+CR_API cr_status cr_dual_step(cr_ctx *c, int iters) {
+    if (!c || iters < 0) {
+        set_err("bad argument to cr_dual_step");
+        return CR_EINVAL;
+    }
+    int left = iters;
+    const int G = c->opt.graph_iters;
+    if (G > 0 && left >= G + (int)(c->k & 1)) {
+        if (c->k & 1) {  // graphs start at an even iteration count
+            CR_TRY(enqueue_iteration(c, c->k + 1, nullptr, nullptr));
+            ++c->k;
+            --left;
+        }
+        CR_TRY(build_graph(c));
+        while (left >= G) {
+            CR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+            c->k += G;
+            left -= G;
+        }
+    }
+    while (left > 0) {
+        CR_TRY(enqueue_iteration(c, c->k + 1, nullptr, nullptr));
+        ++c->k;
+        --left;
+    }
+    return CR_OK;
+}
+
+CR_API cr_status cr_dual_step_timed(cr_ctx *c, int iters, float *sweep_ms, float *total_ms) {
+    if (!c || iters < 0) {
+        set_err("bad argument to cr_dual_step_timed");
+        return CR_EINVAL;
+    }
+    std::vector<cudaEvent_t> evs(2 * (size_t)iters + 1);
+    for (auto &e : evs) CR_CUDA(cudaEventCreate(&e));
+    cr_status s = CR_OK;
+    cudaEvent_t start = evs[2 * (size_t)iters];
+    CR_CUDA(cudaEventRecord(start, c->stream));
+    for (int i = 0; i < iters && s == CR_OK; ++i) {
+        s = enqueue_iteration(c, c->k + 1, evs[2 * i], evs[2 * i + 1]);
+        if (s == CR_OK) ++c->k;
+    }
+    float sw = 0.f, tot = 0.f;
+    if (s == CR_OK) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            set_err("stream failed: %s", cudaGetErrorString(e));
+            s = CR_ECUDA;
+        }
+    }
+    if (s == CR_OK) {
+        for (int i = 0; i < iters; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
+            sw += ms;
+        }
+        if (iters > 0) {
+            // total: from the stream start marker to the end of the last finalize
+            cudaEvent_t endev;
+            cudaEventCreate(&endev);
+            cudaEventRecord(endev, c->stream);
+            cudaEventSynchronize(endev);
+            cudaEventElapsedTime(&tot, start, endev);
+            cudaEventDestroy(endev);
+        }
+    }
+    for (auto &e : evs) cudaEventDestroy(e);
+    if (sweep_ms) *sweep_ms = sw;
+    if (total_ms) *total_ms = tot;
+    return s;
+}
+
+CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
+    if (!c) {
+        set_err("ctx is NULL");
+        return CR_EINVAL;
+    }
+    CertArgs a{};
+    a.N = c->N;
+    a.n = c->n;
+    a.NP = c->NP;
+    a.precision = c->opt.precision;
+    a.row_splits = c->cert_R;
+    a.ldv = c->ldv;
+    a.X = c->X;
+    a.ybar = c->ybar;
+    a.a = c->ha[c->k & 1];
+    a.b = c->hb[c->k & 1];
+    a.yh = c->c_yh;
+    a.yl = c->c_yl;
+    a.uh = c->c_uh;
+    a.ul = c->c_ul;
+    a.xiT = c->c_xiT;
+    a.y64 = c->c_y64;
+    a.u64 = c->c_u64;
+    a.xiT64 = c->c_xiT64;
+    a.xT32 = c->xT32;
+    a.xT64 = c->xT64;
+    a.pmax = c->pmax;
+    a.parg = c->parg;
+    a.pinf = c->pinf;
+    a.blockpart = c->certblk;
+    a.st = c->st;
+    CR_CUDA(launch_cert(a, c->stream));
+    DevState h{};
+    CR_TRY(fetch_state(c, &h));
+    cr_gap_info g{};
+    g.k = h.k;
+    if (h.k == 0) {  // lambda^0 = 0: eta = (ybar, 0), g = r = 0
+        h.last_g = 0.0;
+        h.last_r = 0.0;
+        h.last_lg = 0.0;
+    }
+    g.dual_g = h.last_g;
+    g.primal_r = h.last_r;
+    g.lagr_gap = h.last_lg;
+    const double pairs = (double)c->N * (double)(c->N - 1);
+    g.infeas_norm = sqrt(h.cert_infeas_sq / pairs);
+    const double rden = fabs(g.primal_r) > 1e-300 ? fabs(g.primal_r) : 1e-300;
+    g.rel_gap = std::max(fabs(g.lagr_gap) / rden, g.infeas_norm / c->ybar_rms);
+    g.cert_primal = h.cert_P;
+    g.cert_gap_rel = (h.cert_P - h.last_g) / (fabs(h.cert_P) > 1e-300 ? fabs(h.cert_P) : 1e-300);
+    if (out) *out = g;
+    if (!isfinite(g.dual_g) || !isfinite(g.primal_r) || !isfinite(g.cert_primal)) {
+        set_err("non-finite objective at k = %lld", h.k);
+        return CR_ENUMERIC;
+    }
+    return CR_OK;
+}
+
+CR_API cr_status cr_solve(cr_ctx *c, double tol, long long max_iter, cr_gap_info *out) {
+    if (!c || !(tol >= 0.0) || max_iter < 0) {
+        set_err("bad argument to cr_solve");
+        return CR_EINVAL;
+    }
+    cr_gap_info g{};
+    for (;;) {
+        CR_TRY(cr_gap(c, &g));
+        if (out) *out = g;
+        if (c->k > 0 && g.rel_gap <= tol) return CR_OK;
+        if (c->k >= max_iter) {
+            set_err("rel_gap %.3e > %.3e after %lld iterations", g.rel_gap, tol, c->k);
+            return CR_ENOTCONV;
+        }
+        const long long step = std::min<long long>(c->opt.check_every, max_iter - c->k);
+        CR_TRY(cr_dual_step(c, (int)step));
+    }
+}
+
+CR_API cr_status cr_primal(const cr_ctx *c, double *y, double *xi) {
+    if (!c) {
+        set_err("ctx is NULL");
+        return CR_EINVAL;
+    }
+    CR_CUDA(launch_primal(c->N, c->n, c->ybar, c->ha[c->k & 1], c->hb[c->k & 1], c->st, c->tmp_y, c->tmp_xi,
+                          c->stream));
+    if (y) CR_CUDA(cudaMemcpyAsync(y, c->tmp_y, sizeof(double) * c->N, cudaMemcpyDefault, c->stream));
+    if (xi)
+        CR_CUDA(cudaMemcpyAsync(xi, c->tmp_xi, sizeof(double) * c->N * c->n, cudaMemcpyDefault, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
+
+CR_API cr_status cr_lambda(const cr_ctx *c, long long row0, long long rows, double *out, long long ld) {
+    if (!c || !out || row0 < 0 || rows < 0 || row0 + rows > c->N || ld < c->N) {
+        set_err("bad argument to cr_lambda");
+        return CR_EINVAL;
+    }
+    if (rows == 0) return CR_OK;
+    const void *lam = c->lam[c->k & 1];  // lambda^k lives in lam[k & 1] (lam[0] = lambda^0 at k = 0)
+    cudaPointerAttributes at{};
+    bool dev = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
+               (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (dev) {
+        CR_CUDA(launch_lambda_to_f64(lam, !is_f64(c), c->N, c->ld, row0, rows, out, ld, c->stream));
+        CR_CUDA(cudaStreamSynchronize(c->stream));
+        return CR_OK;
+    }
+    // host destination: convert through a bounded device staging buffer
+    const long long per = std::max<long long>(1, (64LL << 20) / (8LL * c->N));
+    double *stage = nullptr;
+    CR_CUDA(cudaMalloc(&stage, sizeof(double) * std::min(per, rows) * c->N));
+    cr_status s = CR_OK;
+    for (long long r = 0; r < rows && s == CR_OK; r += per) {
+        const long long cnt = std::min(per, rows - r);
+        cudaError_t e = launch_lambda_to_f64(lam, !is_f64(c), c->N, c->ld, row0 + r, cnt, stage, c->N, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(out + r * ld, sizeof(double) * ld, stage, sizeof(double) * c->N,
+                                  sizeof(double) * c->N, cnt, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            set_err("lambda copy failed: %s", cudaGetErrorString(e));
+            s = CR_ECUDA;
+        }
+    }
+    cudaFree(stage);
+    return s;
+}
+
+CR_API cr_status cr_lipschitz(const cr_ctx *c, double *L) {
+    if (!c || !L) {
+        set_err("bad argument to cr_lipschitz");
+        return CR_EINVAL;
+    }
+    *L = c->L;
+    return CR_OK;
+}
+
+CR_API long long cr_iterations(const cr_ctx *c) { return c ? c->k : -1; }
+
+CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
+    if (!c || !buf || len <= 0) {
+        set_err("bad argument to cr_describe");
+        return CR_EINVAL;
+    }
+    const double tsz = is_f64(c) ? 8.0 : 4.0;
+    const double pairs = (double)c->N * (double)(c->N - 1);
+    snprintf(buf, (size_t)len,
+             "{\"N\": %d, \"n\": %d, \"NP\": %d, \"precision\": %d, \"ld\": %lld, \"rows_per_item\": %d, "
+             "\"row_blocks\": %d, \"col_splits\": %d, \"cols_per_split\": %d, \"grid\": %d, "
+             "\"ctas_per_sm\": %d, \"sms\": %d, \"pairs\": %.0f, \"lambda_bytes_per_iter\": %.0f, "
+             "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d}",
+             c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
+             pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters);
+    return CR_OK;
+}
+
+CR_API void cr_destroy(cr_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+CR_API const char *cr_strerror(cr_status s) {
+    switch (s) {
+        case CR_OK: return "ok";
+        case CR_EINVAL: return "invalid argument";
+        case CR_ENOMEM: return "out of memory";
+        case CR_ECUDA: return "CUDA error";
+        case CR_ENOTCONV: return "not converged";
+        case CR_ETIMEOUT: return "device wait timed out";
+        case CR_ENUMERIC: return "non-finite result";
+        case CR_EUNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+CR_API const char *cr_last_error(void) { return g_err; }
+
+CR_API int cr_version(void) { return 100; }
+
+}  // extern "C"

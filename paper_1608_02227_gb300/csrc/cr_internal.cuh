@@ -1,0 +1,161 @@
+// cr_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+//
+// Data layout in HBM for one instance (N points in R^n, NP = n rounded up to a
+// kernel bucket, ld = N rounded up to 32, ldv = N rounded up to 128):
+//   lam[0], lam[1]   N x ld   multipliers (T = float or double), ping-pong:
+//                              iteration k reads lam[(k-1)&1] = lambda^{k-1} and
+//                              lam[k&1] = lambda^{k-2}, and writes lambda^k over
+//                              lam[k&1].  Columns >= N and the diagonal stay 0.
+//   xT               NP x ldv  points, transposed (component-major), zero padded
+//   row side         uh, ul (ldv), xiT (NP x ldv): u_i = y_i - xi_i . x_i and xi_i
+//                              of eta(lambda~^k); FP32 mode splits u = uh + ul
+//   column side      yh, yl (ldv): y_j of eta(lambda~^k), split hi + lo
+//   hist_a[2], hist_b[2]       C^T lambda^{k-1}, C^T lambda^{k-2} (FP64, N and N x n)
+//   rowpart          S x N x (NP+1)   per column split: sum_j lambda_ij x_j, sum_j lambda_ij
+//   colpart          RB x ld          per row block: sum_i lambda_ij
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cr.h"
+
+namespace cr {
+
+constexpr int kChunk = 128;  // columns of Lambda per chunk (32 lanes x 4 columns)
+constexpr int kLogCap = 4096;
+
+// Device-resident scalars of one context.
+struct DevState {
+    double t;           // t_k for the iteration about to run (t_1 = 1)
+    double beta;        // beta_k of the sweep about to run
+    double s;           // step 1/L
+    double gamma;
+    long long k;        // completed iterations
+    unsigned int fin_counter;   // last-block counter of the finalize kernel
+    unsigned int cert_counter;  // last-block counter of the certificate kernel
+    double last_g, last_r, last_lg;      // scalars of lambda^k
+    double cert_P, cert_infeas_sq;       // last certificate
+    int accelerate;
+    int pad;
+};
+
+inline int bucket_np(int n) {
+    static const int b[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+    for (int v : b)
+        if (n <= v) return v;
+    return -1;
+}
+
+inline long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- sweep (S2)
+struct SweepArgsF {
+    const float *P;          // lambda^{k-1}
+    float *Q;                // lambda^{k-2} in, lambda^k out
+    long long ld;            // leading dimension of P, Q
+    int N;
+    int row_blocks;          // RB = ceil(N / ROWS)
+    int col_splits;          // S
+    int cols_per_split;      // multiple of kChunk
+    long long ldv;           // leading dimension of the transposed vectors
+    const float *xT;         // NP x ldv
+    const float *yh, *yl;    // column side
+    const float *uh, *ul;    // row side
+    const float *xiT;        // NP x ldv
+    const DevState *st;
+    float *rowpart;          // S x N x (NP+1)
+    float *colpart;          // RB x ld
+};
+
+struct SweepArgsD {
+    const double *P;
+    double *Q;
+    long long ld;
+    int N;
+    int row_blocks;
+    int col_splits;
+    int cols_per_split;
+    long long ldv;
+    const double *xT;
+    const double *y;
+    const double *u;
+    const double *xiT;
+    const DevState *st;
+    double *rowpart;
+    double *colpart;
+};
+
+struct SweepConfig {
+    int rows;      // rows of Lambda per work item (CTA tile height)
+    int threads;   // threads per CTA
+    size_t smem;   // dynamic shared memory bytes
+};
+
+// Returns false if NP has no instantiation.
+bool sweep_config_f(int np, SweepConfig *cfg);
+bool sweep_config_d(int np, SweepConfig *cfg);
+cudaError_t launch_sweep_f(int np, const SweepArgsF &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep_d(int np, const SweepArgsD &a, int grid, cudaStream_t s);
+cudaError_t sweep_occupancy_f(int np, int *blocks_per_sm);
+cudaError_t sweep_occupancy_d(int np, int *blocks_per_sm);
+
+// ---------------------------------------------------------------- finalize + recovery (S1, S3)
+struct FinArgs {
+    int N, n, NP;
+    int precision;           // 0: FP64 vectors, else FP32 vectors
+    int col_splits, row_blocks;
+    long long ld, ldv;
+    const void *rowpart;     // float or double, S x N x (NP+1)
+    const void *colpart;     // float or double, RB x ld
+    const double *X;         // N x n FP64
+    const double *ybar;
+    double *a_new, *b_new;   // C^T lambda^k (written)
+    const double *a_old, *b_old;  // C^T lambda^{k-1}
+    // recovery outputs for the next sweep
+    float *yh, *yl, *uh, *ul, *xiT;      // FP32 mode
+    double *y64, *u64, *xiT64;           // FP64 mode
+    const float *xT32;                   // FP32 points (u uses the rounded xi and x)
+    double *blockpart;       // gridDim x 3
+    double *log;             // kLogCap x 3
+    DevState *st;
+    int init;                // 1: no partials, a = b = 0 (builds eta(lambda^0))
+};
+cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s);
+
+// eta(lambda^k) from the history: y = ybar + a, xi = b / gamma (FP64, row-major)
+cudaError_t launch_primal(int N, int n, const double *ybar, const double *a, const double *b,
+                          const DevState *st, double *y, double *xi, cudaStream_t s);
+
+// ---------------------------------------------------------------- certificate (S4)
+struct CertArgs {
+    int N, n, NP;
+    int precision;
+    int row_splits;          // R
+    long long ldv;
+    const double *X, *ybar;
+    const double *a, *b;     // C^T lambda^k
+    // vectors of eta(lambda^k) built by the prep kernel
+    float *yh, *yl, *uh, *ul, *xiT;  // FP32
+    double *y64, *u64, *xiT64;       // FP64
+    const float *xT32;
+    const double *xT64;
+    // partial results per (row split, column)
+    double *pmax; int *parg; double *pinf;   // R x N
+    double *blockpart;
+    DevState *st;
+};
+cudaError_t launch_cert(const CertArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- Lipschitz (S0)
+// Returns max_l lambda_max(sum_j (x_l - x_j)(x_l - x_j)^T) = sigma_max(A2)^2.
+cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStream_t s);
+
+// ---------------------------------------------------------------- helpers
+cudaError_t launch_transpose_points(const double *X, int N, int n, int NP, long long ldv,
+                                    float *xT32, double *xT64, cudaStream_t s);
+cudaError_t launch_lambda_to_f64(const void *lam, int is_f32, int N, long long ld, long long row0,
+                                 long long rows, double *out, long long ldo, cudaStream_t s);
+cudaError_t launch_check_finite(const double *v, long long count, int *flag, cudaStream_t s);
+
+}  // namespace cr

@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h
+(CPU only: no compute call is made without a GPU)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1608_02227_gb300 as crgb
+from paper_1608_02227_gb300 import _capi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"CR_API\s+[\w\s\*]+?\b(cr_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _capi.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("cr_create", "cr_dual_step", "cr_solve", "cr_primal", "cr_gap", "cr_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _capi.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s(cr_\w+)$", out, flags=re.M))
+    missing = _declared() - exported
+    assert not missing, missing
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_the_header():
+    assert _declared() <= set(_capi.symbols()) | set()
+    assert set(_capi.symbols()) <= _declared()
+
+
+def test_host_only_calls(lib):
+    o = crgb.default_options()
+    assert o.gamma == 1e-4 and o.precision == crgb.CR_FP32 and o.accelerate == 1
+    assert lib.cr_version() >= 100
+    assert lib.cr_strerror(0) == b"ok"
+    assert lib.cr_strerror(1) == b"invalid argument"
+    with pytest.raises(TypeError):
+        crgb.default_options(no_such_option=1)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(ImportError):
+        _capi.load(str(tmp_path / "nope.so"))
