@@ -215,7 +215,9 @@ cr_status build_graph(cr_ctx *c) {
     cudaGraph_t g = nullptr;
     CR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cr_status s = CR_OK;
-    for (int i = 0; i < len && s == CR_OK; ++i) s = enqueue_iteration(c, 2 + i /* even start */, nullptr, nullptr);
+    // replays start when an even number of iterations is done, so the first captured
+    // iteration has the odd index k + 1 (reads lam[0], writes lam[1])
+    for (int i = 0; i < len && s == CR_OK; ++i) s = enqueue_iteration(c, 1 + i, nullptr, nullptr);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (s != CR_OK) {
         if (g) cudaGraphDestroy(g);
