@@ -163,6 +163,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="lse_N20000_n20")
+    ap.add_argument("--N", type=int, default=0, help="shrink the workload to its first N points (profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -187,6 +188,8 @@ def main():
     prec = {"fp32": crgb.CR_FP32, "fp64": crgb.CR_FP64, "tf32": crgb.CR_MIXED_TF32}[args.precision]
     spec = dict(cr_synth.WORKLOADS[args.workload])
     spec["seed"] = spec.get("seed", 0) + rank
+    if args.N:
+        spec["N"] = args.N
     inst = cr_synth.make_instance(**spec)
     N, n = inst.N, inst.n
     pairs = N * (N - 1)

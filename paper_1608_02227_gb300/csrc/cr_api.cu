@@ -3,6 +3,8 @@
 // iteration blocks, the solve loop and the result copies.
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -69,6 +71,9 @@ struct cr_ctx {
     int *flag = nullptr;
     // sweep shape
     int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
+    bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
+    CUtensorMap tm_lam[2];
+    TmaMaps tm{};
     // graph of graph_iters iterations starting at an even k
     cudaGraphExec_t gexec = nullptr;
     int glen = 0;
@@ -153,6 +158,22 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.rowpart = (double *)c->rowpart;
         a.colpart = (double *)c->colpart;
         CR_CUDA(launch_sweep_d(c->NP, a, c->grid, c->stream));
+    } else if (c->tma) {
+        TmaSweepArgs a{};
+        a.Q = (float *)c->lam[Q];
+        a.ld = c->ld;
+        a.N = c->N;
+        a.row_blocks = c->RB;
+        a.col_splits = c->S;
+        a.cols_per_split = c->cps;
+        a.st = c->st;
+        a.rowpart = (float *)c->rowpart;
+        a.colpart = (float *)c->colpart;
+        a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
+        TmaMaps m = c->tm;
+        m.P = &c->tm_lam[P];
+        m.Q = &c->tm_lam[Q];
+        CR_CUDA(launch_sweep_tma(c->NP, m, a, c->grid, c->stream));
     } else {
         SweepArgsF a{};
         a.P = (const float *)c->lam[P];
@@ -272,10 +293,23 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         set_err("no sweep kernel for n = %d", n);
         return CR_EINVAL;
     }
-    c->rows = cfg.rows;
+    // FP32 runs the TMA-pipelined sweep; CR_SWEEP=simple selects the plain FP32 kernel
+    // (same arithmetic, loads through registers) for A/B measurements.
+    const char *variant = getenv("CR_SWEEP");
+    c->tma = !f64 && !(variant && strcmp(variant, "simple") == 0);
+    c->rows = c->tma ? sweep_tma_rows(c->NP) : cfg.rows;
     c->RB = (N + c->rows - 1) / c->rows;
-    CR_CUDA(f64 ? sweep_occupancy_d(c->NP, &c->occ) : sweep_occupancy_f(c->NP, &c->occ));
-    if (c->occ < 1) c->occ = 1;
+    if (c->tma)
+        CR_CUDA(sweep_tma_occupancy(c->NP, &c->occ));
+    else
+        CR_CUDA(f64 ? sweep_occupancy_d(c->NP, &c->occ) : sweep_occupancy_f(c->NP, &c->occ));
+    if (c->occ < 1) {
+        int d[4] = {0, 0, 0, 0};
+        if (c->tma) sweep_tma_diag(d);
+        set_err("the sweep kernel for n = %d does not fit on this device (occupancy 0; regs %d, max threads %d, "
+                "smem %d, threads %d)", n, d[0], d[1], d[2], d[3]);
+        return CR_EUNSUPPORTED;
+    }
     choose_split(c);
 
     CR_TRY(dev_alloc(c, &c->X, (size_t)N * n));
@@ -310,17 +344,22 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(cudaMemsetAsync(c->u64, 0, vec * sizeof(double), c->stream));
     } else {
         CR_TRY(dev_alloc(c, &c->xT32, tvec));
-        float **f[] = {&c->yh, &c->yl, &c->uh, &c->ul, &c->c_yh, &c->c_yl, &c->c_uh, &c->c_ul};
+        // hi and lo halves adjacent ([2][ldv]) so one 2-D TMA box fetches both
+        float **f[] = {&c->yh, &c->uh, &c->c_yh, &c->c_uh};
         for (float **p : f) {
-            CR_TRY(dev_alloc(c, p, vec));
-            CR_CUDA(cudaMemsetAsync(*p, 0, vec * sizeof(float), c->stream));
+            CR_TRY(dev_alloc(c, p, 2 * vec));
+            CR_CUDA(cudaMemsetAsync(*p, 0, 2 * vec * sizeof(float), c->stream));
         }
+        c->yl = c->yh + vec;
+        c->ul = c->uh + vec;
+        c->c_yl = c->c_yh + vec;
+        c->c_ul = c->c_uh + vec;
         CR_TRY(dev_alloc(c, &c->xiT, tvec));
         CR_TRY(dev_alloc(c, &c->c_xiT, tvec));
         CR_CUDA(cudaMemsetAsync(c->xiT, 0, tvec * sizeof(float), c->stream));
         CR_CUDA(cudaMemsetAsync(c->c_xiT, 0, tvec * sizeof(float), c->stream));
     }
-    CR_CUDA(launch_transpose_points(c->X, N, n, c->NP, c->ldv, c->xT32, c->xT64, c->stream));
+    CR_CUDA(launch_transpose_points(c->X, N, n, c->NP, c->ldv, c->xT32, c->xT64, nullptr, c->stream));
 
     // step constant (Section 3 "Preprocess" + Eq. (lischitz))
     if (c->opt.lipschitz > 0.0) {
@@ -353,6 +392,14 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(cudaMemsetAsync(c->ha[i], 0, sizeof(double) * N, c->stream));
         CR_CUDA(cudaMemsetAsync(c->hb[i], 0, sizeof(double) * N * n, c->stream));
     }
+    if (c->tma) {
+        for (int i = 0; i < 2; ++i)
+            CR_CUDA(make_tmap_2d(&c->tm_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, kChunk, c->rows));
+        CR_CUDA(make_tmap_2d(&c->tm.X, c->xT32, c->ldv, c->NP, c->ldv, kChunk, c->NP));
+        CR_CUDA(make_tmap_2d(&c->tm.Y, c->yh, c->ldv, 2, c->ldv, kChunk, 2));
+        CR_CUDA(make_tmap_2d(&c->tm.Xi, c->xiT, c->ldv, c->NP, c->ldv, c->rows, c->NP));
+        CR_CUDA(make_tmap_2d(&c->tm.U, c->uh, c->ldv, 2, c->ldv, c->rows, 2));
+    }
     const size_t rp = (size_t)c->S * N * (c->NP + 1), cp = (size_t)c->RB * c->ld;
     if (f64) {
         double *a, *b;
@@ -368,7 +415,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         c->colpart = b;
     }
     const int gN = (N + 255) / 256;
-    CR_TRY(dev_alloc(c, &c->finblk, (size_t)gN * 3));
+    CR_TRY(dev_alloc(c, &c->finblk, (size_t)finalize_blocks(N) * 3));
     CR_TRY(dev_alloc(c, &c->certblk, (size_t)gN * 2));
     CR_TRY(dev_alloc(c, &c->log, (size_t)kLogCap * 3));
     CR_TRY(dev_alloc(c, &c->st, 1));
@@ -627,6 +674,10 @@ CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
     CR_CUDA(launch_cert(a, c->stream));
     DevState h{};
     CR_TRY(fetch_state(c, &h));
+    if (h.err) {
+        set_err("a device-side wait ran out (status %d) before iteration %lld", h.err, h.k + 1);
+        return CR_ETIMEOUT;
+    }
     cr_gap_info g{};
     g.k = h.k;
     if (h.k == 0) {  // lambda^0 = 0: eta = (ybar, 0), g = r = 0
@@ -743,9 +794,11 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              "{\"N\": %d, \"n\": %d, \"NP\": %d, \"precision\": %d, \"ld\": %lld, \"rows_per_item\": %d, "
              "\"row_blocks\": %d, \"col_splits\": %d, \"cols_per_split\": %d, \"grid\": %d, "
              "\"ctas_per_sm\": %d, \"sms\": %d, \"pairs\": %.0f, \"lambda_bytes_per_iter\": %.0f, "
-             "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d}",
+             "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d, "
+             "\"sweep\": \"%s\"}",
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
-             pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters);
+             pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters,
+             c->tma ? "tma" : (is_f64(c) ? "fp64" : "simple"));
     return CR_OK;
 }
 

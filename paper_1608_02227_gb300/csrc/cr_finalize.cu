@@ -11,85 +11,99 @@
 namespace cr {
 namespace {
 
-constexpr int kFinThreads = 256;
-
 __device__ __forceinline__ void split_hi_lo(double v, float *hi, float *lo) {
     const float h = (float)v;
     *hi = h;
     *lo = (float)(v - (double)h);
 }
 
-// Deterministic block sum of three doubles (fixed tree order).
-__device__ void block_sum3(double v0, double v1, double v2, double *out3) {
-    __shared__ double sh[3][kFinThreads];
-    const int t = threadIdx.x;
-    sh[0][t] = v0;
-    sh[1][t] = v1;
-    sh[2][t] = v2;
-    __syncthreads();
-    for (int w = kFinThreads / 2; w > 0; w >>= 1) {
-        if (t < w) {
-            sh[0][t] += sh[0][t + w];
-            sh[1][t] += sh[1][t + w];
-            sh[2][t] += sh[2][t + w];
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        out3[0] = sh[0][0];
-        out3[1] = sh[1][0];
-        out3[2] = sh[2][0];
-    }
-}
+constexpr int kFX = 32;   // points per CTA
+constexpr int kFY = 8;    // slices per point (row blocks, components)
 
+// One CTA finalizes 32 points; the 8 warps split each point's reductions (row blocks of
+// the column sums, components of b) and combine them through shared memory in a fixed
+// order, so the result does not depend on scheduling.
 template <typename PT>
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinArgs a) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int l = blockIdx.x * kFX + tx;
+    const bool valid = l < a.N;
     DevState *st = a.st;
     const double gamma = st->gamma;
     const double tk = st->t;
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));           // Step 3
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));               // Step 3
     const double beta = (st->accelerate && !a.init) ? (tk - 1.0) / tn : 0.0;  // Step 4 coefficient
     const PT *rowp = reinterpret_cast<const PT *>(a.rowpart);
     const PT *colp = reinterpret_cast<const PT *>(a.colpart);
     const int W = a.NP + 1;
+    __shared__ double s_c[kFY][kFX], s_u[kFY][kFX], s_b[kFY][kFX];
+    __shared__ double s_r[kFX];
 
-    double saa = 0.0, say = 0.0, sbb = 0.0;
-    if (l < a.N) {
-        // C^T lambda^k: a_l = c_l - r_l, b_l = r_l x_l - sum_j lambda_lj x_j
-        double r = 0.0, c = 0.0;
-        if (!a.init) {
-            for (int s = 0; s < a.col_splits; ++s) r += (double)rowp[((long long)s * a.N + l) * W + a.NP];
-            for (int b = 0; b < a.row_blocks; ++b) c += (double)colp[(long long)b * a.ld + l];
+    // C^T lambda^k: a_l = c_l - r_l (Definition 1), c_l from the per-row-block partials
+    double c = 0.0;
+    if (valid && !a.init) {
+        // eight independent loads in flight per thread, added in row-block order
+        int b = ty;
+        for (; b + 7 * kFY < a.row_blocks; b += 8 * kFY) {
+            PT v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = colp[(long long)(b + u * kFY) * a.ld + l];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) c += (double)v[u];
         }
-        const double al = c - r;
-        a.a_new[l] = al;
-        saa = al * al;
-        say = al * a.ybar[l];
-        // Step 1 for the next iteration: eta(lambda~^{k+1}) with
-        // C^T lambda~^{k+1} = (1 + beta) C^T lambda^k - beta C^T lambda^{k-1}
-        const double at = (1.0 + beta) * al - beta * a.a_old[l];
-        const double y = a.ybar[l] + at;
-        double u = y;
-        for (int k = 0; k < a.n; ++k) {
+        for (; b < a.row_blocks; b += kFY) c += (double)colp[(long long)b * a.ld + l];
+    }
+    s_c[ty][tx] = c;
+    if (ty == 0) {
+        double r = 0.0;
+        if (valid && !a.init)
+            for (int sp = 0; sp < a.col_splits; ++sp) r += (double)rowp[((long long)sp * a.N + l) * W + a.NP];
+        s_r[tx] = r;
+    }
+    __syncthreads();
+    const double r = s_r[tx];
+    double cc = 0.0;
+#pragma unroll
+    for (int y = 0; y < kFY; ++y) cc += s_c[y][tx];
+    const double al = cc - r;
+    // b_l = r_l x_l - sum_j lambda_lj x_j, and Step 1 of the next iteration:
+    // C^T lambda~^{k+1} = (1 + beta) C^T lambda^k - beta C^T lambda^{k-1}; xi = b~ / gamma
+    double upart = 0.0, bpart = 0.0;
+    if (valid) {
+        for (int k = ty; k < a.n; k += kFY) {
             double Bk = 0.0;
             if (!a.init)
-                for (int s = 0; s < a.col_splits; ++s) Bk += (double)rowp[((long long)s * a.N + l) * W + k];
+                for (int sp = 0; sp < a.col_splits; ++sp) Bk += (double)rowp[((long long)sp * a.N + l) * W + k];
             const double xk = a.X[(long long)l * a.n + k];
             const double bl = r * xk - Bk;
             a.b_new[(long long)l * a.n + k] = bl;
-            sbb += bl * bl;
+            bpart += bl * bl;
             const double bt = (1.0 + beta) * bl - beta * a.b_old[(long long)l * a.n + k];
             const double xi = bt / gamma;
             if (a.precision == CR_FP64) {
                 a.xiT64[(long long)k * a.ldv + l] = xi;
-                u -= xi * xk;
+                upart -= xi * xk;
             } else {
                 // the sweep sees the rounded xi and x; u is formed from exactly those
                 const float xf = (float)xi;
                 a.xiT[(long long)k * a.ldv + l] = xf;
-                u -= (double)xf * (double)a.xT32[(long long)k * a.ldv + l];
+                upart -= (double)xf * (double)a.xT32[(long long)k * a.ldv + l];
             }
+        }
+    }
+    s_u[ty][tx] = upart;
+    s_b[ty][tx] = bpart;
+    __syncthreads();
+    double saa = 0.0, say = 0.0, sbb = 0.0;
+    if (ty == 0 && valid) {
+        a.a_new[l] = al;
+        const double at = (1.0 + beta) * al - beta * a.a_old[l];
+        const double y = a.ybar[l] + at;
+        double u = y;
+#pragma unroll
+        for (int q = 0; q < kFY; ++q) {
+            u += s_u[q][tx];
+            sbb += s_b[q][tx];
         }
         if (a.precision == CR_FP64) {
             a.y64[l] = y;
@@ -98,19 +112,27 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinArgs a) 
             split_hi_lo(y, a.yh + l, a.yl + l);
             split_hi_lo(u, a.uh + l, a.ul + l);
         }
+        saa = al * al;
+        say = al * a.ybar[l];
     }
     if (a.init) return;
 
-    __shared__ double part[3];
-    block_sum3(saa, say, sbb, part);
     __shared__ bool last;
-    if (threadIdx.x == 0) {
-        a.blockpart[blockIdx.x * 3 + 0] = part[0];
-        a.blockpart[blockIdx.x * 3 + 1] = part[1];
-        a.blockpart[blockIdx.x * 3 + 2] = part[2];
-        __threadfence();
-        const unsigned ticket = atomicAdd(&st->fin_counter, 1u);
-        last = (ticket == gridDim.x - 1);
+    if (ty == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            saa += __shfl_xor_sync(0xffffffffu, saa, o);
+            say += __shfl_xor_sync(0xffffffffu, say, o);
+            sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+        }
+        if (tx == 0) {
+            a.blockpart[blockIdx.x * 3 + 0] = saa;
+            a.blockpart[blockIdx.x * 3 + 1] = say;
+            a.blockpart[blockIdx.x * 3 + 2] = sbb;
+            __threadfence();
+            const unsigned ticket = atomicAdd(&st->fin_counter, 1u);
+            last = (ticket == gridDim.x - 1);
+        }
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
@@ -150,7 +172,7 @@ __global__ void primal_kernel(int N, int n, const double *ybar, const double *av
 }
 
 __global__ void transpose_points_kernel(const double *X, int N, int n, int NP, long long ldv,
-                                        float *xT32, double *xT64) {
+                                        float *xT32, double *xT64, float *xT2) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= (long long)NP * ldv) return;
     const int k = (int)(q / ldv);
@@ -158,6 +180,10 @@ __global__ void transpose_points_kernel(const double *X, int N, int n, int NP, l
     const double v = (k < n && l < N) ? X[l * n + k] : 0.0;
     if (xT32) xT32[q] = (float)v;
     if (xT64) xT64[q] = v;
+    if (xT2) {  // [NP][2 ldv]: every x_lk twice, (x_lk, x_lk) pairs for packed FMAs
+        xT2[(long long)k * 2 * ldv + 2 * l] = (float)v;
+        xT2[(long long)k * 2 * ldv + 2 * l + 1] = (float)v;
+    }
 }
 
 __global__ void lambda_to_f64_kernel(const void *lam, int is_f32, int N, long long ld, long long row0,
@@ -178,12 +204,14 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 }  // namespace
 
+int finalize_blocks(int N) { return (int)blocks_for(N, kFX); }
+
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s) {
-    const unsigned g = blocks_for(a.N, kFinThreads);
+    const unsigned g = blocks_for(a.N, kFX);
     if (a.precision == CR_FP64)
-        finalize_kernel<double><<<g, kFinThreads, 0, s>>>(a);
+        finalize_kernel<double><<<g, kFX * kFY, 0, s>>>(a);
     else
-        finalize_kernel<float><<<g, kFinThreads, 0, s>>>(a);
+        finalize_kernel<float><<<g, kFX * kFY, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -195,9 +223,9 @@ cudaError_t launch_primal(int N, int n, const double *ybar, const double *a, con
 }
 
 cudaError_t launch_transpose_points(const double *X, int N, int n, int NP, long long ldv, float *xT32,
-                                    double *xT64, cudaStream_t s) {
+                                    double *xT64, float *xT2, cudaStream_t s) {
     transpose_points_kernel<<<blocks_for((long long)NP * ldv, 256), 256, 0, s>>>(X, N, n, NP, ldv, xT32,
-                                                                                  xT64);
+                                                                                  xT64, xT2);
     return cudaGetLastError();
 }
 

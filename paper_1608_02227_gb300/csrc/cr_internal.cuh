@@ -15,6 +15,7 @@
 //   colpart          RB x ld          per row block: sum_i lambda_ij
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,7 +38,7 @@ struct DevState {
     double last_g, last_r, last_lg;      // scalars of lambda^k
     double cert_P, cert_infeas_sq;       // last certificate
     int accelerate;
-    int pad;
+    int err;            // CR_ETIMEOUT when a bounded device-side wait ran out
 };
 
 inline int bucket_np(int n) {
@@ -100,6 +101,30 @@ cudaError_t launch_sweep_d(int np, const SweepArgsD &a, int grid, cudaStream_t s
 cudaError_t sweep_occupancy_f(int np, int *blocks_per_sm);
 cudaError_t sweep_occupancy_d(int np, int *blocks_per_sm);
 
+// FP32 sweep with the TMA / mbarrier pipeline (cr_sweep_tma.cu)
+struct TmaSweepArgs {
+    float *Q;                // lambda^k is written here (the buffer that held lambda^{k-2})
+    long long ld;
+    int N;
+    int row_blocks, col_splits, cols_per_split;
+    const DevState *st;
+    float *rowpart;          // S x N x (NP+1)
+    float *colpart;          // RB x ld
+    int *err;
+};
+struct TmaMaps {
+    const CUtensorMap *P, *Q;            // lambda^{k-1}, lambda^{k-2}: [N][ld], box 128 x R
+    CUtensorMap X, Y, Xi, U;             // xT [NP][ldv] box 128 x NP; y hi/lo [2][ldv] box 128 x 2;
+                                         // xiT [NP][ldv] box R x NP; u hi/lo [2][ldv] box R x 2
+                                         // (R = sweep_tma_rows(NP))
+};
+cudaError_t launch_sweep_tma(int np, const TmaMaps &m, const TmaSweepArgs &a, int grid, cudaStream_t s);
+cudaError_t sweep_tma_occupancy(int np, int *blocks_per_sm);
+int sweep_tma_rows(int np);
+void sweep_tma_diag(int *v4);  // regs, max threads, smem, threads of a kernel that did not fit   // rows per work item of the TMA sweep for bucket np
+cudaError_t make_tmap_2d(CUtensorMap *tm, const float *base, long long cols, long long rows, long long ld,
+                         int box_cols, int box_rows);
+
 // ---------------------------------------------------------------- finalize + recovery (S1, S3)
 struct FinArgs {
     int N, n, NP;
@@ -122,6 +147,7 @@ struct FinArgs {
     int init;                // 1: no partials, a = b = 0 (builds eta(lambda^0))
 };
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s);
+int finalize_blocks(int N);   // CTAs of the finalize kernel (size of its block-partial buffer / 3)
 
 // eta(lambda^k) from the history: y = ybar + a, xi = b / gamma (FP64, row-major)
 cudaError_t launch_primal(int N, int n, const double *ybar, const double *a, const double *b,
@@ -153,7 +179,7 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
 
 // ---------------------------------------------------------------- helpers
 cudaError_t launch_transpose_points(const double *X, int N, int n, int NP, long long ldv,
-                                    float *xT32, double *xT64, cudaStream_t s);
+                                    float *xT32, double *xT64, float *xT2, cudaStream_t s);
 cudaError_t launch_lambda_to_f64(const void *lam, int is_f32, int N, long long ld, long long row0,
                                  long long rows, double *out, long long ldo, cudaStream_t s);
 cudaError_t launch_check_finite(const double *v, long long count, int *flag, cudaStream_t s);

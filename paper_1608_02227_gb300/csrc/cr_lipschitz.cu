@@ -61,19 +61,30 @@ __global__ void scatter_kernel(const double *X, int N, int n, const double *mean
     }
 }
 
-// cyclic Jacobi on the n x n symmetric Sc (one thread): D (n), V (n x n, columns = vectors)
+// cyclic Jacobi on the n x n symmetric Sc, one warp: every lane recomputes the rotation
+// and updates one row/column index r of A and of the accumulated vectors V (columns =
+// eigenvectors).  D (n) and V (n x n) are written at the end.
 __global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     __shared__ double A[CR_MAX_N * CR_MAX_N];
     __shared__ double Q[CR_MAX_N * CR_MAX_N];
-    for (int i = 0; i < n * n; ++i) A[i] = Sc[i];
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) Q[i * n + j] = (i == j) ? 1.0 : 0.0;
+    const int lane = threadIdx.x;
+    for (int i = lane; i < n * n; i += 32) {
+        A[i] = Sc[i];
+        Q[i] = (i / n == i % n) ? 1.0 : 0.0;
+    }
+    __syncwarp();
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0.0, dia = 0.0;
-        for (int p = 0; p < n; ++p) {
-            dia += A[p * n + p] * A[p * n + p];
-            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+        for (int i = lane; i < n * n; i += 32) {
+            const int p = i / n, q = i % n;
+            if (p == q)
+                dia += A[i] * A[i];
+            else if (p < q)
+                off += A[i] * A[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
         }
         if (off <= 1e-32 * dia || off == 0.0) break;
         for (int p = 0; p < n; ++p)
@@ -83,25 +94,26 @@ __global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
                 const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
                 const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                 const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < n; ++r) {  // A <- A J
-                    const double arp = A[r * n + p], arq = A[r * n + q];
-                    A[r * n + p] = c * arp - s * arq;
-                    A[r * n + q] = s * arp + c * arq;
+                __syncwarp();
+                if (lane < n) {  // A <- A J (columns p, q)
+                    const double arp = A[lane * n + p], arq = A[lane * n + q];
+                    A[lane * n + p] = c * arp - s * arq;
+                    A[lane * n + q] = s * arp + c * arq;
+                    const double qrp = Q[lane * n + p], qrq = Q[lane * n + q];
+                    Q[lane * n + p] = c * qrp - s * qrq;
+                    Q[lane * n + q] = s * qrp + c * qrq;
                 }
-                for (int r = 0; r < n; ++r) {  // A <- J^T A
-                    const double apr = A[p * n + r], aqr = A[q * n + r];
-                    A[p * n + r] = c * apr - s * aqr;
-                    A[q * n + r] = s * apr + c * aqr;
+                __syncwarp();
+                if (lane < n) {  // A <- J^T A (rows p, q)
+                    const double apr = A[p * n + lane], aqr = A[q * n + lane];
+                    A[p * n + lane] = c * apr - s * aqr;
+                    A[q * n + lane] = s * apr + c * aqr;
                 }
-                for (int r = 0; r < n; ++r) {  // Q <- Q J
-                    const double qrp = Q[r * n + p], qrq = Q[r * n + q];
-                    Q[r * n + p] = c * qrp - s * qrq;
-                    Q[r * n + q] = s * qrp + c * qrq;
-                }
+                __syncwarp();
             }
     }
-    for (int i = 0; i < n; ++i) D[i] = A[i * n + i];
-    for (int i = 0; i < n * n; ++i) V[i] = Q[i];
+    for (int i = lane; i < n; i += 32) D[i] = A[i * n + i];
+    for (int i = lane; i < n * n; i += 32) V[i] = Q[i];
 }
 
 __global__ void secular_kernel(const double *X, int N, int n, const double *mean, const double *D,
@@ -164,7 +176,7 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
     cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     mean_kernel<<<n, kT, 0, s>>>(X, N, n, mean);
     scatter_kernel<<<n * (n + 1) / 2, kT, 0, s>>>(X, N, n, mean, Sc);
-    jacobi_kernel<<<1, 32, 0, s>>>(Sc, n, D, V);
+    jacobi_kernel<<<1, 32, 0, s>>>(Sc, n, D, V);  // one warp
     secular_kernel<<<(N + kT - 1) / kT, kT, 0, s>>>(X, N, n, mean, D, V, best);
     unsigned long long bits = 0;
     e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);
