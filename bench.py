@@ -157,6 +157,53 @@ def cpu_baseline(workload):
             "sample": f"first {Ns} points of {workload}, {iters} FP64 oracle iterations ({dt:.1f} s)"}
 
 
+def run_batch(args):
+    """Batched solves: `count` instances (N log-uniform in [100, 4000], n in {2..16},
+    f0 = ||x||^2 + N(0, 0.1^2)), all submitted at t = 0 into one cr_batch, each retired at
+    rel_gap <= tol.  Reports solves/s, lambda-pair updates/s and completion-time p50/p99,
+    against the same instances solved one after another with the single-instance path."""
+    import torch
+
+    import paper_1608_02227_gb300 as crgb
+
+    torch.cuda.set_device(0)
+    insts = cr_synth.batch_workload(args.count, seed=0)
+    check = 100
+    max_iter = 200000
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_at = {}
+    pairs = 0.0
+    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check) as b:
+        ids = [b.add(i.X, i.ybar, tol=args.tol, max_iter=max_iter) for i in insts]
+        t_setup = time.perf_counter() - t0
+        width = b.autotune(2)
+        active = len(ids)
+        while active:
+            active = b.step(check)
+            now = time.perf_counter() - t0
+            for i in ids:
+                if i not in done_at and b.poll(i)[0]:
+                    done_at[i] = now
+        infos = [b.poll(i) for i in ids]
+    wall = time.perf_counter() - t0
+    for inst, (done, st, info) in zip(insts, infos):
+        pairs += inst.N * (inst.N - 1) * info["k"]
+    lat = sorted(done_at.values())
+    conv = sum(1 for d, st, _ in infos if st == 0)
+    line = {"metric": "solves_per_s", "value": len(insts) / wall, "unit": "solves/s", "n_gpus": 1,
+            "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch{len(insts)}_sqnorm_N100-4000_n2-16", "gamma": GAMMA, "tol": args.tol,
+                       "check_every": check, "tile_cols": width},
+            "converged": conv, "lambda_pairs_per_s": pairs / wall, "setup_s": t_setup, "wall_s": wall,
+            "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                          "max": lat[-1]},
+            "iterations": {"min": min(i[2]["k"] for i in infos), "max": max(i[2]["k"] for i in infos)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,11 +214,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "batch"],
+                    help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances")
+    ap.add_argument("--count", type=int, default=256, help="instances in --mode batch")
+    ap.add_argument("--tol", type=float, default=1e-4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
 
     import torch
 

@@ -146,6 +146,55 @@ CR_API long long cr_iterations(const cr_ctx *ctx);
 /* Releases every resource of the context (NULL is ignored). */
 CR_API void cr_destroy(cr_ctx *ctx);
 
+/* ------------------------------------------------------------------------------------
+ * Batched solving: many independent instances (uneven N and n) iterate together.  Every
+ * iteration is one persistent TMA sweep launch per point-dimension bucket over a device
+ * work-list of (instance, 32-row block, column split) items -- the buckets run as parallel
+ * branches of a captured CUDA graph -- followed by one finalize launch over all instances.
+ * Each instance keeps its own multipliers, step constant, t_k and iteration count, and is
+ * retired at its own convergence check (the K = N method of Figure "papg" per instance).
+ * A batch is bound to one stream and is not thread-safe.
+ * ------------------------------------------------------------------------------------ */
+typedef struct cr_batch cr_batch;
+
+/* opt: NULL for the defaults (precision must be CR_FP32; graph_iters is the number of
+ * iterations per captured graph; check_every the iterations between checks in
+ * cr_batch_run).  stream: as in cr_create. */
+CR_API cr_status cr_batch_create(const cr_options *opt, void *stream, cr_batch **out);
+
+/* Adds one instance (X: N x n, ybar: N; host or device; copied).  It is retired once a
+ * check finds rel_gap <= rel_gap_tol (status CR_OK) or after max_iter iterations
+ * (status CR_ENOTCONV).  *id receives its handle (>= 0). */
+CR_API cr_status cr_batch_add(cr_batch *b, const double *X, const double *ybar, long long N, int n,
+                              double rel_gap_tol, long long max_iter, int *id);
+
+/* Runs `iters` iterations of every active instance, then checks every active instance
+ * and retires the converged ones.  *active (may be NULL) receives how many remain. */
+CR_API cr_status cr_batch_step(cr_batch *b, int iters, int *active);
+
+/* Repeats cr_batch_step(opt.check_every) until no instance is active. */
+CR_API cr_status cr_batch_run(cr_batch *b);
+
+/* Retirement state of instance id: *done = 1 once retired; *status = CR_OK (converged),
+ * CR_ENOTCONV (max_iter) or an error; *info = its last convergence record. */
+CR_API cr_status cr_batch_poll(cr_batch *b, int id, int *done, int *status, cr_gap_info *info);
+
+/* eta(lambda^k) of instance id, as cr_primal. */
+CR_API cr_status cr_batch_primal(cr_batch *b, int id, double *y, double *xi);
+
+/* Releases the device memory of instance id (active or retired); the id stays invalid. */
+CR_API cr_status cr_batch_remove(cr_batch *b, int id);
+
+/* Device bytes that an instance of N points in n dimensions takes in a batch. */
+CR_API long long cr_batch_instance_bytes(long long N, int n);
+
+/* Times `iters` iterations of the active instances for each column-split width in
+ * {512, 1024, 2048, 4096, whole rows} and keeps the fastest (the iterations count as
+ * real iterations).  *tile_cols (may be NULL) receives the chosen width. */
+CR_API cr_status cr_batch_autotune(cr_batch *b, int iters, int *tile_cols);
+
+CR_API void cr_batch_destroy(cr_batch *b);
+
 CR_API const char *cr_strerror(cr_status s);
 CR_API const char *cr_last_error(void);
 CR_API int cr_version(void);

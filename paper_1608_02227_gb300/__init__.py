@@ -19,7 +19,7 @@ __all__ = [
     "CR_FP64", "CR_FP32", "CR_MIXED_TF32", "CR_L_HESSIAN", "CR_L_PAPER", "CR_MAX_N", "CRError",
     "default_options", "cr_create", "cr_dual_step", "cr_dual_step_timed", "cr_solve", "cr_primal",
     "cr_gap", "cr_lambda", "cr_lipschitz", "cr_iterations", "cr_describe", "cr_destroy", "Solver",
-    "library_path",
+    "library_path", "Batch", "cr_batch_instance_bytes",
 ]
 
 
@@ -203,6 +203,77 @@ class Solver:
         if self.ctx:
             cr_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cr_batch_instance_bytes(N: int, n: int) -> int:
+    return int(_lib().cr_batch_instance_bytes(int(N), int(n)))
+
+
+class Batch:
+    """Many independent instances iterated together (cr_batch_* of include/cr.h)."""
+
+    def __init__(self, stream=None, **options):
+        self.opt = default_options(**options)
+        self.handle = ctypes.c_void_p()
+        check(_lib().cr_batch_create(ctypes.byref(self.opt), _stream_handle(stream), ctypes.byref(self.handle)))
+        self.shapes = {}
+
+    def add(self, X, ybar, tol=1e-4, max_iter=100000):
+        xp, xk = _ptr(X)
+        yp, yk = _ptr(ybar)
+        N, n = int(xk.shape[0]), int(xk.shape[1])
+        i = ctypes.c_int()
+        check(_lib().cr_batch_add(self.handle, xp, yp, N, n, float(tol), int(max_iter), ctypes.byref(i)))
+        self.shapes[i.value] = (N, n)
+        return i.value
+
+    def step(self, iters):
+        a = ctypes.c_int()
+        check(_lib().cr_batch_step(self.handle, int(iters), ctypes.byref(a)))
+        return a.value
+
+    def run(self):
+        check(_lib().cr_batch_run(self.handle))
+
+    def poll(self, i):
+        done = ctypes.c_int()
+        st = ctypes.c_int()
+        g = cr_gap_info()
+        check(_lib().cr_batch_poll(self.handle, int(i), ctypes.byref(done), ctypes.byref(st), ctypes.byref(g)))
+        return bool(done.value), int(st.value), g.as_dict()
+
+    def primal(self, i):
+        N, n = self.shapes[i]
+        y = np.empty(N)
+        xi = np.empty((N, n))
+        check(_lib().cr_batch_primal(self.handle, int(i), ctypes.c_void_p(y.ctypes.data),
+                                     ctypes.c_void_p(xi.ctypes.data)))
+        return y, xi
+
+    def remove(self, i):
+        check(_lib().cr_batch_remove(self.handle, int(i)))
+
+    def autotune(self, iters=4):
+        w = ctypes.c_int()
+        check(_lib().cr_batch_autotune(self.handle, int(iters), ctypes.byref(w)))
+        return w.value
+
+    def close(self):
+        if self.handle:
+            _lib().cr_batch_destroy(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self

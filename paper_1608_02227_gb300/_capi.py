@@ -74,6 +74,18 @@ _SIGS = [
     ("cr_lipschitz", ctypes.c_int, [_vp, _dp]),
     ("cr_iterations", ctypes.c_longlong, [_vp]),
     ("cr_destroy", None, [_vp]),
+    ("cr_batch_create", ctypes.c_int, [ctypes.POINTER(cr_options), _vp, ctypes.POINTER(_vp)]),
+    ("cr_batch_add", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+    ("cr_batch_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("cr_batch_run", ctypes.c_int, [_vp]),
+    ("cr_batch_poll", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(cr_gap_info)]),
+    ("cr_batch_primal", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    ("cr_batch_remove", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("cr_batch_instance_bytes", ctypes.c_longlong, [ctypes.c_longlong, ctypes.c_int]),
+    ("cr_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("cr_batch_destroy", None, [_vp]),
     ("cr_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("cr_last_error", ctypes.c_char_p, []),
     ("cr_version", ctypes.c_int, []),

@@ -12,11 +12,11 @@
 #include <new>
 #include <vector>
 
-#include "cr_internal.cuh"
+#include "cr_host.h"
 
 using namespace cr;
 
-namespace {
+namespace crh {
 
 thread_local char g_err[512] = "";
 
@@ -26,81 +26,6 @@ void set_err(const char *fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
 }
-
-#define CR_CUDA(call)                                                                      \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess) {                                                           \
-            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-            return e_ == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;                 \
-        }                                                                                  \
-    } while (0)
-
-}  // namespace
-
-struct cr_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int N = 0, n = 0, NP = 0;
-    long long ld = 0, ldv = 0;
-    cr_options opt{};
-    double L = 0.0, a2s2 = 0.0, ybar_rms = 1.0;
-    long long k = 0;  // iterations enqueued
-    int sms = 0;
-
-    std::vector<void *> allocs;
-    double *X = nullptr, *ybar = nullptr;
-    float *xT32 = nullptr;
-    double *xT64 = nullptr;
-    void *lam[2] = {nullptr, nullptr};
-    double *ha[2] = {nullptr, nullptr}, *hb[2] = {nullptr, nullptr};
-    float *yh = nullptr, *yl = nullptr, *uh = nullptr, *ul = nullptr, *xiT = nullptr;
-    double *y64 = nullptr, *u64 = nullptr, *xiT64 = nullptr;
-    void *rowpart = nullptr, *colpart = nullptr;
-    double *finblk = nullptr, *certblk = nullptr, *log = nullptr;
-    DevState *st = nullptr;
-    // certificate buffers
-    float *c_yh = nullptr, *c_yl = nullptr, *c_uh = nullptr, *c_ul = nullptr, *c_xiT = nullptr;
-    double *c_y64 = nullptr, *c_u64 = nullptr, *c_xiT64 = nullptr;
-    double *pmax = nullptr, *pinf = nullptr;
-    int *parg = nullptr;
-    int cert_R = 1;
-    // primal scratch
-    double *tmp_y = nullptr, *tmp_xi = nullptr;
-    int *flag = nullptr;
-    // sweep shape
-    int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
-    bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
-    CUtensorMap tm_lam[2];
-    TmaMaps tm{};
-    // graph of graph_iters iterations starting at an even k
-    cudaGraphExec_t gexec = nullptr;
-    int glen = 0;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-};
-
-namespace {
-
-template <typename T>
-cr_status dev_alloc(cr_ctx *c, T **p, size_t count) {
-    void *q = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
-    if (e != cudaSuccess) {
-        set_err("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
-    }
-    c->allocs.push_back(q);
-    *p = reinterpret_cast<T *>(q);
-    return CR_OK;
-}
-
-#define CR_TRY(x)                       \
-    do {                                \
-        cr_status s_ = (x);             \
-        if (s_ != CR_OK) return s_;     \
-    } while (0)
 
 bool is_f64(const cr_ctx *c) { return c->opt.precision == CR_FP64; }
 
@@ -473,7 +398,71 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     return CR_OK;
 }
 
-}  // namespace
+// Enqueues the pass over all pairs for eta(lambda^k) (certificate + infeasibility).
+cr_status gap_launch(cr_ctx *c) {
+    CertArgs a{};
+    a.N = c->N;
+    a.n = c->n;
+    a.NP = c->NP;
+    a.precision = c->opt.precision;
+    a.row_splits = c->cert_R;
+    a.ldv = c->ldv;
+    a.X = c->X;
+    a.ybar = c->ybar;
+    a.a = c->ha[c->k & 1];
+    a.b = c->hb[c->k & 1];
+    a.yh = c->c_yh;
+    a.yl = c->c_yl;
+    a.uh = c->c_uh;
+    a.ul = c->c_ul;
+    a.xiT = c->c_xiT;
+    a.y64 = c->c_y64;
+    a.u64 = c->c_u64;
+    a.xiT64 = c->c_xiT64;
+    a.xT32 = c->xT32;
+    a.xT64 = c->xT64;
+    a.pmax = c->pmax;
+    a.parg = c->parg;
+    a.pinf = c->pinf;
+    a.blockpart = c->certblk;
+    a.st = c->st;
+    CR_CUDA(launch_cert(a, c->stream));
+    return CR_OK;
+}
+
+// Convergence record from the device scalars (after gap_launch and a copy of the state).
+cr_status gap_finish(const cr_ctx *c, DevState h, cr_gap_info *out) {
+    if (h.err) {
+        set_err("a device-side wait ran out (status %d) before iteration %lld", h.err, h.k + 1);
+        return CR_ETIMEOUT;
+    }
+    cr_gap_info g{};
+    g.k = h.k;
+    if (h.k == 0) {  // lambda^0 = 0: eta = (ybar, 0), g = r = 0
+        h.last_g = 0.0;
+        h.last_r = 0.0;
+        h.last_lg = 0.0;
+    }
+    g.dual_g = h.last_g;
+    g.primal_r = h.last_r;
+    g.lagr_gap = h.last_lg;
+    const double pairs = (double)c->N * (double)(c->N - 1);
+    g.infeas_norm = sqrt(h.cert_infeas_sq / pairs);
+    const double rden = fabs(g.primal_r) > 1e-300 ? fabs(g.primal_r) : 1e-300;
+    g.rel_gap = std::max(fabs(g.lagr_gap) / rden, g.infeas_norm / c->ybar_rms);
+    g.cert_primal = h.cert_P;
+    g.cert_gap_rel = (h.cert_P - h.last_g) / (fabs(h.cert_P) > 1e-300 ? fabs(h.cert_P) : 1e-300);
+    if (out) *out = g;
+    if (!isfinite(g.dual_g) || !isfinite(g.primal_r) || !isfinite(g.cert_primal)) {
+        set_err("non-finite objective at k = %lld", h.k);
+        return CR_ENUMERIC;
+    }
+    return CR_OK;
+}
+
+}  // namespace crh
+
+using namespace crh;
 
 extern "C" {
 
@@ -645,61 +634,10 @@ CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
         set_err("ctx is NULL");
         return CR_EINVAL;
     }
-    CertArgs a{};
-    a.N = c->N;
-    a.n = c->n;
-    a.NP = c->NP;
-    a.precision = c->opt.precision;
-    a.row_splits = c->cert_R;
-    a.ldv = c->ldv;
-    a.X = c->X;
-    a.ybar = c->ybar;
-    a.a = c->ha[c->k & 1];
-    a.b = c->hb[c->k & 1];
-    a.yh = c->c_yh;
-    a.yl = c->c_yl;
-    a.uh = c->c_uh;
-    a.ul = c->c_ul;
-    a.xiT = c->c_xiT;
-    a.y64 = c->c_y64;
-    a.u64 = c->c_u64;
-    a.xiT64 = c->c_xiT64;
-    a.xT32 = c->xT32;
-    a.xT64 = c->xT64;
-    a.pmax = c->pmax;
-    a.parg = c->parg;
-    a.pinf = c->pinf;
-    a.blockpart = c->certblk;
-    a.st = c->st;
-    CR_CUDA(launch_cert(a, c->stream));
+    CR_TRY(gap_launch(c));
     DevState h{};
     CR_TRY(fetch_state(c, &h));
-    if (h.err) {
-        set_err("a device-side wait ran out (status %d) before iteration %lld", h.err, h.k + 1);
-        return CR_ETIMEOUT;
-    }
-    cr_gap_info g{};
-    g.k = h.k;
-    if (h.k == 0) {  // lambda^0 = 0: eta = (ybar, 0), g = r = 0
-        h.last_g = 0.0;
-        h.last_r = 0.0;
-        h.last_lg = 0.0;
-    }
-    g.dual_g = h.last_g;
-    g.primal_r = h.last_r;
-    g.lagr_gap = h.last_lg;
-    const double pairs = (double)c->N * (double)(c->N - 1);
-    g.infeas_norm = sqrt(h.cert_infeas_sq / pairs);
-    const double rden = fabs(g.primal_r) > 1e-300 ? fabs(g.primal_r) : 1e-300;
-    g.rel_gap = std::max(fabs(g.lagr_gap) / rden, g.infeas_norm / c->ybar_rms);
-    g.cert_primal = h.cert_P;
-    g.cert_gap_rel = (h.cert_P - h.last_g) / (fabs(h.cert_P) > 1e-300 ? fabs(h.cert_P) : 1e-300);
-    if (out) *out = g;
-    if (!isfinite(g.dual_g) || !isfinite(g.primal_r) || !isfinite(g.cert_primal)) {
-        set_err("non-finite objective at k = %lld", h.k);
-        return CR_ENUMERIC;
-    }
-    return CR_OK;
+    return gap_finish(c, h, out);
 }
 
 CR_API cr_status cr_solve(cr_ctx *c, double tol, long long max_iter, cr_gap_info *out) {

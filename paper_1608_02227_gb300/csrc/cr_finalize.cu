@@ -24,9 +24,9 @@ constexpr int kFY = 8;    // slices per point (row blocks, components)
 // the column sums, components of b) and combine them through shared memory in a fixed
 // order, so the result does not depend on scheduling.
 template <typename PT>
-__global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
+__device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, const int nblk) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int l = blockIdx.x * kFX + tx;
+    const int l = blk * kFX + tx;
     const bool valid = l < a.N;
     DevState *st = a.st;
     const double gamma = st->gamma;
@@ -126,19 +126,19 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
             sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
         }
         if (tx == 0) {
-            a.blockpart[blockIdx.x * 3 + 0] = saa;
-            a.blockpart[blockIdx.x * 3 + 1] = say;
-            a.blockpart[blockIdx.x * 3 + 2] = sbb;
+            a.blockpart[blk * 3 + 0] = saa;
+            a.blockpart[blk * 3 + 1] = say;
+            a.blockpart[blk * 3 + 2] = sbb;
             __threadfence();
             const unsigned ticket = atomicAdd(&st->fin_counter, 1u);
-            last = (ticket == gridDim.x - 1);
+            last = (ticket == (unsigned)nblk - 1u);
         }
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
         double aa = 0.0, ay = 0.0, bb = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
+        for (int b = 0; b < nblk; ++b) {
             aa += ((volatile double *)a.blockpart)[b * 3 + 0];
             ay += ((volatile double *)a.blockpart)[b * 3 + 1];
             bb += ((volatile double *)a.blockpart)[b * 3 + 2];
@@ -161,6 +161,46 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
         st->fin_counter = 0u;
         __threadfence();
     }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
+    finalize_body<PT>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched finalize: one CTA per (instance, 32-point block) of the work-list.
+__global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDesc *d, const FinItem *items) {
+    const FinItem it = items[blockIdx.x];
+    const InstDesc &D = d[it.inst];
+    const long long k = D.st->k + 1;  // index of the iteration being finalized
+    FinArgs a{};
+    a.N = D.N;
+    a.n = D.n;
+    a.NP = D.NP;
+    a.precision = CR_FP32;
+    a.col_splits = D.col_splits;
+    a.row_blocks = D.row_blocks;
+    a.ld = D.ld;
+    a.ldv = D.ldv;
+    a.rowpart = D.rowpart;
+    a.colpart = D.colpart;
+    a.X = D.X;
+    a.ybar = D.ybar;
+    a.a_new = D.ha[k & 1];
+    a.b_new = D.hb[k & 1];
+    a.a_old = D.ha[(k - 1) & 1];
+    a.b_old = D.hb[(k - 1) & 1];
+    a.yh = D.yh;
+    a.yl = D.yl;
+    a.uh = D.uh;
+    a.ul = D.ul;
+    a.xiT = D.xiT;
+    a.xT32 = D.xT32;
+    a.blockpart = D.finblk;
+    a.log = D.log;
+    a.st = D.st;
+    a.init = 0;
+    finalize_body<float>(a, it.block, D.fin_blocks);
 }
 
 __global__ void primal_kernel(int N, int n, const double *ybar, const double *av, const double *bv,
@@ -205,6 +245,12 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 }  // namespace
 
 int finalize_blocks(int N) { return (int)blocks_for(N, kFX); }
+
+cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    finalize_batch_kernel<<<nitems, kFX * kFY, 0, s>>>(d, items);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s) {
     const unsigned g = blocks_for(a.N, kFX);

@@ -1,0 +1,94 @@
+// cr_host.h -- host-side context shared by the single-instance (cr_api.cu) and batched
+// (cr_batch.cu) front ends.  Not part of the ABI.
+#pragma once
+
+#include <vector>
+
+#include "cr_internal.cuh"
+
+using namespace cr;
+
+struct cr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int N = 0, n = 0, NP = 0;
+    long long ld = 0, ldv = 0;
+    cr_options opt{};
+    double L = 0.0, a2s2 = 0.0, ybar_rms = 1.0;
+    long long k = 0;  // iterations enqueued
+    int sms = 0;
+
+    std::vector<void *> allocs;
+    double *X = nullptr, *ybar = nullptr;
+    float *xT32 = nullptr;
+    double *xT64 = nullptr;
+    void *lam[2] = {nullptr, nullptr};
+    double *ha[2] = {nullptr, nullptr}, *hb[2] = {nullptr, nullptr};
+    float *yh = nullptr, *yl = nullptr, *uh = nullptr, *ul = nullptr, *xiT = nullptr;
+    double *y64 = nullptr, *u64 = nullptr, *xiT64 = nullptr;
+    void *rowpart = nullptr, *colpart = nullptr;
+    double *finblk = nullptr, *certblk = nullptr, *log = nullptr;
+    DevState *st = nullptr;
+    // certificate buffers
+    float *c_yh = nullptr, *c_yl = nullptr, *c_uh = nullptr, *c_ul = nullptr, *c_xiT = nullptr;
+    double *c_y64 = nullptr, *c_u64 = nullptr, *c_xiT64 = nullptr;
+    double *pmax = nullptr, *pinf = nullptr;
+    int *parg = nullptr;
+    int cert_R = 1;
+    // primal scratch
+    double *tmp_y = nullptr, *tmp_xi = nullptr;
+    int *flag = nullptr;
+    // sweep shape
+    int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
+    bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
+    CUtensorMap tm_lam[2];
+    TmaMaps tm{};
+    // graph of graph_iters iterations starting at an even k
+    cudaGraphExec_t gexec = nullptr;
+    int glen = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace crh {
+
+void set_err(const char *fmt, ...);
+
+#define CR_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;                 \
+        }                                                                                  \
+    } while (0)
+
+#define CR_TRY(x)                       \
+    do {                                \
+        cr_status s_ = (x);             \
+        if (s_ != CR_OK) return s_;     \
+    } while (0)
+
+template <typename T>
+cr_status dev_alloc(cr_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_err("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
+    }
+    c->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return CR_OK;
+}
+
+bool is_f64(const cr_ctx *c);
+void choose_split(cr_ctx *c);
+cr_status create_impl(cr_ctx *c, const double *X, const double *ybar);
+cr_status fetch_state(const cr_ctx *c, DevState *h);
+cr_status enqueue_iteration(cr_ctx *c, long long k, cudaEvent_t e0, cudaEvent_t e1);
+cr_status gap_launch(cr_ctx *c);
+cr_status gap_finish(const cr_ctx *c, DevState h, cr_gap_info *out);
+
+}  // namespace crh

@@ -125,6 +125,33 @@ void sweep_tma_diag(int *v4);  // regs, max threads, smem, threads of a kernel t
 cudaError_t make_tmap_2d(CUtensorMap *tm, const float *base, long long cols, long long rows, long long ld,
                          int box_cols, int box_rows);
 
+// Batched sweep: one descriptor per instance (device memory, tensor maps included) and a
+// work-list of items; the P/Q parity of an instance is its device counter k modulo 2.
+struct WorkItem {
+    int inst, rb, sp;
+};
+struct InstDesc {
+    CUtensorMap tm_lam[2];               // lam[0], lam[1]: [N][ld], box 128 x R
+    CUtensorMap tm_x, tm_y, tm_xi, tm_u; // as in TmaMaps
+    float *lam[2];
+    long long ld, ldv;
+    int N, n, NP, cols_per_split;
+    int row_blocks, col_splits, fin_blocks, inst_id;
+    DevState *st;
+    float *rowpart, *colpart;
+    const double *X, *ybar;
+    double *ha[2], *hb[2];
+    float *yh, *yl, *uh, *ul, *xiT;
+    const float *xT32;
+    double *finblk, *log;
+};
+cudaError_t launch_sweep_tma_batch(int np, const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
+                                   cudaStream_t s);
+struct FinItem {
+    int inst, block;
+};
+cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s);
+
 // ---------------------------------------------------------------- finalize + recovery (S1, S3)
 struct FinArgs {
     int N, n, NP;

@@ -97,12 +97,82 @@ struct TmaShape {
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)XB * ROWBUF_FLOATS * 4 + 256;
 };
 
-template <int NP>
-__global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
-    sweep_tma_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
-                     const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-                     const __grid_constant__ CUtensorMap tmXi, const __grid_constant__ CUtensorMap tmU,
-                     const TmaSweepArgs a) {
+// Per-item view of the data a work item needs (tensor maps, pointers, tile bounds).
+struct ItemView {
+    const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
+    float *Qp;
+    long long ld, c0, c1;
+    int N, i0, rb, sp;
+    float *rowpart, *colpart;
+    const DevState *st;
+};
+
+// One instance: the tensor maps are kernel parameters, items tile [0, N) x [0, ld).
+struct SrcSingle {
+    const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
+    TmaSweepArgs a;
+    __device__ __forceinline__ int count() const { return a.row_blocks * a.col_splits; }
+    __device__ __forceinline__ void prefetch() const {
+        prefetch_tmap(P);
+        prefetch_tmap(Q);
+        prefetch_tmap(X);
+        prefetch_tmap(Y);
+        prefetch_tmap(Xi);
+        prefetch_tmap(U);
+    }
+    __device__ __forceinline__ ItemView view(int item, int rows) const {
+        ItemView v;
+        v.P = P; v.Q = Q; v.X = X; v.Y = Y; v.Xi = Xi; v.U = U;
+        v.Qp = a.Q;
+        v.ld = a.ld;
+        v.N = a.N;
+        v.rb = item / a.col_splits;
+        v.sp = item - v.rb * a.col_splits;
+        v.i0 = v.rb * rows;
+        v.c0 = (long long)v.sp * a.cols_per_split;
+        v.c1 = min(v.c0 + (long long)a.cols_per_split, a.ld);
+        v.rowpart = a.rowpart;
+        v.colpart = a.colpart;
+        v.st = a.st;
+        return v;
+    }
+};
+
+// Many instances: per-instance descriptors (with their tensor maps) in global memory and a
+// work-list of (instance, row block, column split).  The ping-pong parity of each instance
+// comes from its own device iteration counter, so a captured graph replays correctly for
+// instances that joined at any iteration.
+struct SrcBatch {
+    const InstDesc *d;
+    const WorkItem *w;
+    int n;
+    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ void prefetch() const {}
+    __device__ __forceinline__ ItemView view(int item, int rows) const {
+        const WorkItem wi = w[item];
+        const InstDesc &D = d[wi.inst];
+        const int par = (int)(D.st->k & 1);
+        ItemView v;
+        v.P = &D.tm_lam[par];
+        v.Q = &D.tm_lam[par ^ 1];
+        v.X = &D.tm_x; v.Y = &D.tm_y; v.Xi = &D.tm_xi; v.U = &D.tm_u;
+        v.Qp = D.lam[par ^ 1];
+        v.ld = D.ld;
+        v.N = D.N;
+        v.rb = wi.rb;
+        v.sp = wi.sp;
+        v.i0 = wi.rb * rows;
+        v.c0 = (long long)wi.sp * D.cols_per_split;
+        v.c1 = min(v.c0 + (long long)D.cols_per_split, D.ld);
+        v.rowpart = D.rowpart;
+        v.colpart = D.colpart;
+        v.st = D.st;
+        return v;
+    }
+};
+
+template <int NP, class Src>
+__device__ __forceinline__ void sweep_body(const Src &src, int *err) {
     using S = TmaShape<NP>;
     constexpr int MR = S::MR, CW = S::CW, STAGES = S::STAGES, XB = S::XB, kRowsT = S::kRowsT;
     extern __shared__ unsigned char smem_raw[];
@@ -116,7 +186,7 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
     volatile int *abort_flag = ticket + STAGES;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int items = a.row_blocks * a.col_splits;
+    const int items = src.count();
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -132,24 +202,18 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
     if (warp == CW) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            prefetch_tmap(&tmP);
-            prefetch_tmap(&tmQ);
-            prefetch_tmap(&tmX);
-            prefetch_tmap(&tmY);
-            prefetch_tmap(&tmXi);
-            prefetch_tmap(&tmU);
+            src.prefetch();
             uint32_t fill = 0, item_no = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_no) {
-                const int rb = item / a.col_splits, sp = item - rb * a.col_splits;
-                const int i0 = rb * kRowsT;
-                const long long c0 = (long long)sp * a.cols_per_split;
-                const long long c1 = min(c0 + (long long)a.cols_per_split, a.ld);
+                const ItemView v = src.view(item, kRowsT);
+                const int i0 = v.i0;
+                const long long c0 = v.c0, c1 = v.c1;
                 bool first = true;
                 for (long long j0 = c0; j0 < c1; j0 += kChunk, ++fill) {
                     const int s = fill % STAGES;
                     const uint32_t ph = (fill / STAGES) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.err)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) {
                         ok = false;
                         break;
                     }
@@ -157,14 +221,14 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
                     mbar_arrive_expect_tx(&full[s], S::TX_CHUNK + (first ? S::TX_ROWS : 0));
                     if (first) {
                         float *rbuf = rowbuf + (item_no % XB) * S::ROWBUF_FLOATS;
-                        tma_load_2d(rbuf, &tmXi, &full[s], i0, 0);
-                        tma_load_2d(rbuf + NP * kRowsT, &tmU, &full[s], i0, 0);
+                        tma_load_2d(rbuf, v.Xi, &full[s], i0, 0);
+                        tma_load_2d(rbuf + NP * kRowsT, v.U, &full[s], i0, 0);
                         first = false;
                     }
-                    tma_load_2d(st, &tmP, &full[s], (int)j0, i0);
-                    tma_load_2d(st + S::TILE, &tmQ, &full[s], (int)j0, i0);
-                    tma_load_2d(st + 2 * S::TILE, &tmX, &full[s], (int)j0, 0);
-                    tma_load_2d(st + 2 * S::TILE + NP * kChunk, &tmY, &full[s], (int)j0, 0);
+                    tma_load_2d(st, v.P, &full[s], (int)j0, i0);
+                    tma_load_2d(st + S::TILE, v.Q, &full[s], (int)j0, i0);
+                    tma_load_2d(st + 2 * S::TILE, v.X, &full[s], (int)j0, 0);
+                    tma_load_2d(st + 2 * S::TILE + NP * kChunk, v.Y, &full[s], (int)j0, 0);
                 }
             }
             // drain: every issued copy must land before the CTA exits
@@ -179,16 +243,15 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ consumers
-        const float beta = (float)a.st->beta;
-        const float sstep = (float)a.st->s;
-        const float2 beta2 = make_float2(beta, beta), s2 = make_float2(sstep, sstep);
         const float2 m1 = make_float2(-1.f, -1.f);
         uint32_t fill = 0, item_no = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++item_no) {
-            const int rb = item / a.col_splits, sp = item - rb * a.col_splits;
-            const int i0 = rb * kRowsT;
-            const long long c0 = (long long)sp * a.cols_per_split;
-            const long long c1 = min(c0 + (long long)a.cols_per_split, a.ld);
+            const ItemView v = src.view(item, kRowsT);
+            const int i0 = v.i0, rb = v.rb, sp = v.sp, NN = v.N;
+            const long long c0 = v.c0, c1 = v.c1, ld = v.ld;
+            const float beta = (float)v.st->beta;
+            const float sstep = (float)v.st->s;
+            const float2 beta2 = make_float2(beta, beta), s2 = make_float2(sstep, sstep);
             const float *rbuf = rowbuf + (item_no % XB) * S::ROWBUF_FLOATS;
             const float *xis = rbuf;                  // [NP][kRowsT]
             const float *ush = rbuf + NP * kRowsT;    // [2][kRowsT]: u hi, u lo
@@ -208,7 +271,7 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
             for (long long j0 = c0; j0 < c1; j0 += kChunk, ++fill) {
                 const int s = fill % STAGES;
                 const uint32_t ph = (fill / STAGES) & 1u;
-                const bool ok = mbar_wait(&full[s], ph, abort_flag, a.err);
+                const bool ok = mbar_wait(&full[s], ph, abort_flag, err);
                 float *st = stages + (size_t)s * (S::STAGE_BYTES / 4);
                 if (ok) {
                     float lam[MR][4];
@@ -252,7 +315,7 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
                     }
                     // Steps 4 + 2: lambda~ = P + beta (P - Q); lambda = max(0, lambda~ + s rho)
                     const bool edge = (j0 < (long long)i0 + kRowsT && j0 + kChunk > i0) ||
-                                      (j0 + kChunk > a.N) || (i0 + kRowsT > a.N);
+                                      (j0 + kChunk > NN) || (i0 + kRowsT > NN);
                     float2 cs01 = make_float2(0.f, 0.f), cs23 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int r = 0; r < MR; ++r) {
@@ -273,11 +336,11 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const long long j = j0 + 4 * lane + c;
-                                if (i >= a.N || j >= a.N || j == i) lam[r][c] = 0.f;
+                                if (i >= NN || j >= NN || j == i) lam[r][c] = 0.f;
                             }
                         }
-                        if (4 * lane + j0 < c1 && i0 + rloc + r < a.N)
-                            __stcs(reinterpret_cast<float4 *>(a.Q + (long long)(i0 + rloc + r) * a.ld + j0 + 4 * lane),
+                        if (4 * lane + j0 < c1 && i0 + rloc + r < NN)
+                            __stcs(reinterpret_cast<float4 *>(v.Qp + (long long)(i0 + rloc + r) * ld + j0 + 4 * lane),
                                    make_float4(lam[r][0], lam[r][1], lam[r][2], lam[r][3]));
                         cs01 = __fadd2_rn(cs01, make_float2(lam[r][0], lam[r][1]));
                         cs23 = __fadd2_rn(cs23, make_float2(lam[r][2], lam[r][3]));
@@ -321,16 +384,16 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
                     __threadfence_block();
                     if (ok && !*abort_flag) {
                         const long long jl = j0 + 4 * lane;
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                         for (int w = 0; w < CW; ++w) {
                             const float4 t = *reinterpret_cast<const float4 *>(st + w * MR * kChunk + 4 * lane);
-                            v.x += t.x;
-                            v.y += t.y;
-                            v.z += t.z;
-                            v.w += t.w;
+                            cv.x += t.x;
+                            cv.y += t.y;
+                            cv.z += t.z;
+                            cv.w += t.w;
                         }
-                        if (jl < c1) *reinterpret_cast<float4 *>(a.colpart + (long long)rb * a.ld + jl) = v;
+                        if (jl < c1) *reinterpret_cast<float4 *>(v.colpart + (long long)rb * ld + jl) = cv;
                     }
                     __syncwarp();
                     if (lane == 0) {
@@ -343,8 +406,8 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
 #pragma unroll
             for (int p = 0; p < MR / 2; ++p) {
                 const int ia = i0 + rloc + 2 * p, ib = ia + 1;
-                float *da = a.rowpart + ((long long)sp * a.N + ia) * (NP + 1);
-                float *db = a.rowpart + ((long long)sp * a.N + ib) * (NP + 1);
+                float *da = v.rowpart + ((long long)sp * NN + ia) * (NP + 1);
+                float *db = v.rowpart + ((long long)sp * NN + ib) * (NP + 1);
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
                     float vx = Bp[p][k].x, vy = Bp[p][k].y;
@@ -354,8 +417,8 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
                         vy += __shfl_xor_sync(0xffffffffu, vy, o);
                     }
                     if (lane == 0) {
-                        if (ia < a.N) da[k] = vx;
-                        if (ib < a.N) db[k] = vy;
+                        if (ia < NN) da[k] = vx;
+                        if (ib < NN) db[k] = vy;
                     }
                 }
                 float vx = rs2[p].x, vy = rs2[p].y;
@@ -365,12 +428,30 @@ __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
                     vy += __shfl_xor_sync(0xffffffffu, vy, o);
                 }
                 if (lane == 0) {
-                    if (ia < a.N) da[NP] = vx;
-                    if (ib < a.N) db[NP] = vy;
+                    if (ia < NN) da[NP] = vx;
+                    if (ib < NN) db[NP] = vy;
                 }
             }
         }
     }
+}
+
+
+template <int NP>
+__global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
+    sweep_tma_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
+                     const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                     const __grid_constant__ CUtensorMap tmXi, const __grid_constant__ CUtensorMap tmU,
+                     const TmaSweepArgs a) {
+    SrcSingle src{&tmP, &tmQ, &tmX, &tmY, &tmXi, &tmU, a};
+    sweep_body<NP>(src, a.err);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
+    sweep_tma_batch_kernel(const InstDesc *d, const WorkItem *w, int nitems, int *err) {
+    SrcBatch src{d, w, nitems};
+    sweep_body<NP>(src, err);
 }
 
 #define CR_NP_LIST(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32)
@@ -409,6 +490,31 @@ cudaError_t launch_sweep_tma(int np, const TmaMaps &m, const TmaSweepArgs &a, in
     switch (np) {
 #define CASE(V) \
     case V: return run_tma<V>(m, a, grid, s, nullptr);
+        CR_NP_LIST(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NP>
+cudaError_t run_tma_batch(const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid, cudaStream_t st) {
+    using S = TmaShape<NP>;
+    auto k = sweep_tma_batch_kernel<NP>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k<<<grid, S::THREADS, S::SMEM, st>>>(d, w, nitems, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_tma_batch(int np, const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
+                                   cudaStream_t s) {
+    switch (np) {
+#define CASE(V) \
+    case V: return run_tma_batch<V>(d, w, nitems, err, grid, s);
         CR_NP_LIST(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
