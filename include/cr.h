@@ -140,6 +140,23 @@ CR_API cr_status cr_describe(const cr_ctx *ctx, char *buf, int len);
 /* Returns the step constant L in use. */
 CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
 
+/* Allocation-free computation of the step constant L that cr_create computes (the paper
+ * has no counterpart: this is an interface for callers that must not allocate device
+ * memory at the moment they need L -- e.g. an admission controller that budgets HBM before
+ * reserving it, a framework whose caching allocator owns all of HBM, or a latency-critical
+ * loop where cudaMalloc/cudaFree would synchronise the device).
+ *   X: N x n points, FP64, row-major, DEVICE memory only (host pointers are rejected with
+ *   CR_EINVAL); rule: CR_L_HESSIAN or CR_L_PAPER; stream: cudaStream_t or NULL; *L receives
+ *   the same value cr_create computes for these inputs.  Synchronises the stream.
+ * Limit: 1 <= n <= CR_MAX_N (32); the scratch is a fixed 16.6 KB array in device memory that
+ * every GPU which loads the library holds until the process exits.  No cudaMalloc, cudaFree
+ * or other allocating call is made.  The first call on a device (with that device current)
+ * looks up the array's device address; make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (two streams or threads
+ * at once) race and must be serialised by the caller. */
+CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, int n, double gamma, int rule, void *stream,
+                                      double *L);
+
 /* Iterations taken so far. */
 CR_API long long cr_iterations(const cr_ctx *ctx);
 

@@ -72,6 +72,8 @@ _SIGS = [
                                           ctypes.POINTER(ctypes.c_float)]),
     ("cr_describe", ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int]),
     ("cr_lipschitz", ctypes.c_int, [_vp, _dp]),
+    ("cr_lipschitz_noalloc", ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp,
+                                            _dp]),
     ("cr_iterations", ctypes.c_longlong, [_vp]),
     ("cr_destroy", None, [_vp]),
     ("cr_batch_create", ctypes.c_int, [ctypes.POINTER(cr_options), _vp, ctypes.POINTER(_vp)]),

@@ -13,7 +13,9 @@
 #include <math.h>
 #include <string.h>
 
-#include "cr_internal.cuh"
+#include <mutex>
+
+#include "cr_host.h"
 
 namespace cr {
 namespace {
@@ -190,3 +192,99 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
 }
 
 }  // namespace cr
+
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of the step-constant computation above.
+//
+// Some callers cannot allocate device memory when they need L: a serving front end that
+// budgets HBM exactly and decides admission before reserving anything, code that runs
+// under a framework whose caching allocator owns all of HBM, or latency-critical loops in
+// which cudaMalloc/cudaFree would synchronise the device.  For them the scratch of the
+// four kernels (mean, centred scatter, eigenvectors, eigenvalues, the max word) lives in
+// one fixed array in device memory that every GPU loading this library holds until the
+// process exits.
+// ------------------------------------------------------------------------------------
+namespace {
+
+// mean (n) + scatter (n^2) + eigenvectors (n^2) + eigenvalues (n) + one 64-bit max word,
+// for n <= CR_MAX_N: 2 * 32 * 32 + 2 * 32 + 8 doubles = 16.6 KB.
+constexpr int kLipScratchDoubles = 2 * CR_MAX_N * CR_MAX_N + 2 * CR_MAX_N + 8;
+static __device__ __align__(256) double g_lip_scratch[kLipScratchDoubles];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_lip_mu;
+double *g_lip_addr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, int n, double gamma, int rule,
+                                                void *stream, double *L) {
+    using crh::set_err;
+    if (!X || !L) {
+        set_err("X or L is NULL");
+        return CR_EINVAL;
+    }
+    if (N < 2 || N > (1LL << 30)) {
+        set_err("N = %lld out of range [2, 2^30]", N);
+        return CR_EINVAL;
+    }
+    if (n < 1 || n > CR_MAX_N) {
+        set_err("n = %d exceeds the fixed scratch of cr_lipschitz_noalloc (1 <= n <= %d)", n, CR_MAX_N);
+        return CR_EINVAL;
+    }
+    if (!(gamma > 0.0) || !isfinite(gamma) || (rule != CR_L_HESSIAN && rule != CR_L_PAPER)) {
+        set_err("gamma must be finite and > 0, rule CR_L_HESSIAN or CR_L_PAPER");
+        return CR_EINVAL;
+    }
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, X) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        set_err("X must be device memory (the allocation-free path cannot stage host data)");
+        return CR_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_err("cudaGetDevice failed or device %d out of range: %s", dev, cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
+    double *scr = nullptr;
+    {
+        // first call on this device (with it current): the device address of the array
+        std::lock_guard<std::mutex> lock(g_lip_mu);
+        if (!g_lip_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_lip_scratch);
+            if (e != cudaSuccess || !p) {
+                set_err("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+                return CR_ECUDA;
+            }
+            g_lip_addr[dev] = static_cast<double *>(p);
+        }
+        scr = g_lip_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *mean = scr, *Sc = mean + n, *V = Sc + (size_t)n * n, *D = V + (size_t)n * n;
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(scr + kLipScratchDoubles - 1);
+    // the max word is the only scratch read before it is written: clear it every call
+    e = cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        mean_kernel<<<n, kT, 0, s>>>(X, (int)N, n, mean);
+        scatter_kernel<<<n * (n + 1) / 2, kT, 0, s>>>(X, (int)N, n, mean, Sc);
+        jacobi_kernel<<<1, 32, 0, s>>>(Sc, n, D, V);
+        secular_kernel<<<(unsigned)((N + kT - 1) / kT), kT, 0, s>>>(X, (int)N, n, mean, D, V, best);
+        e = cudaGetLastError();
+    }
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_err("cr_lipschitz_noalloc failed: %s", cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
+    double s2;
+    memcpy(&s2, &bits, sizeof(s2));
+    *L = (rule == CR_L_PAPER) ? (2.0 * (double)N + s2) / gamma : 2.0 * (double)N + s2 / gamma;
+    return CR_OK;
+}

@@ -1,0 +1,50 @@
+"""The allocation-free step-constant entry point (cr_lipschitz_noalloc) against cr_create's L.
+
+This file is collected last on purpose: if the allocation-free path misbehaves, a run that
+stops at the first failure has already run every other test.  It runs correctly both alone
+in a fresh process and after the other tests (the static scratch array is set up on first
+use and cleared where needed on every call).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import cr_synth
+import paper_1608_02227_gb300 as crgb
+from paper_1608_02227_gb300 import _capi
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(X_dev, gamma, rule):
+    lib = _capi.load()
+    L = ctypes.c_double(-1.0)
+    st = lib.cr_lipschitz_noalloc(ctypes.c_void_p(X_dev.data_ptr()), int(X_dev.shape[0]), int(X_dev.shape[1]),
+                                  float(gamma), int(rule), None, ctypes.byref(L))
+    return st, L.value
+
+
+def test_noalloc_matches_cr_create_on_two_calls_in_a_row():
+    import torch
+    cases = [(3000, 20, 1e-4, crgb.CR_L_HESSIAN, "lse"), (777, 7, 1e-3, crgb.CR_L_PAPER, "maxaff")]
+    for N, n, gamma, rule, fam in cases:
+        inst = cr_synth.make_instance(N, n, fam, 0.1, 5)
+        with crgb.Solver(inst.X, inst.ybar, gamma=gamma, lipschitz_rule=rule) as s:
+            L_ref = s.L
+        Xd = torch.tensor(inst.X, device="cuda")
+        st, L = _noalloc(Xd, gamma, rule)
+        assert st == 0, _capi.load().cr_last_error()
+        # same kernels and arithmetic as cr_create: equal within the tests' 1e-10 relative bar
+        assert abs(L - L_ref) <= 1e-10 * L_ref, (N, n, L, L_ref)
+
+
+def test_noalloc_rejects_what_its_scratch_cannot_hold():
+    import torch
+    lib = _capi.load()
+    Xd = torch.zeros((10, 33), dtype=torch.float64, device="cuda")
+    L = ctypes.c_double()
+    assert lib.cr_lipschitz_noalloc(ctypes.c_void_p(Xd.data_ptr()), 10, 33, 1e-4, 0, None, ctypes.byref(L)) == 1
+    assert b"scratch" in lib.cr_last_error()
+    Xh = np.zeros((10, 3))
+    assert lib.cr_lipschitz_noalloc(ctypes.c_void_p(Xh.ctypes.data), 10, 3, 1e-4, 0, None, ctypes.byref(L)) == 1
