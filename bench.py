@@ -204,6 +204,64 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Poisson stream (rate args.rate) of `count` requests: N log-uniform in [200, N_max], n in
+    {2..32}, f0 drawn from {||x||^2, max of 10 affine, log-sum-exp of 8}, noise 0.1; each to
+    rel_gap <= tol (cap 20000 iterations).  Served with continuous batching (60 GB cap), then
+    the same stream on the plain single-instance path (one solve at a time, FIFO, same
+    arrival times, cr_solve with the same check interval)."""
+    import torch
+
+    import paper_1608_02227_gb300 as crgb
+
+    torch.cuda.set_device(0)
+    reqs = cr_synth.serving_stream(args.count, rate=args.rate, seed=0, N_lo=200, N_hi=args.N_max)
+    max_iter, check = 20000, 100
+    # continuous batching
+    t0 = time.perf_counter()
+    with crgb.Server(mem_cap_bytes=60 << 30, max_active=256, gamma=GAMMA, check_every=check,
+                     graph_iters=20) as srv:
+        ids = []
+        for t_arr, inst in reqs:
+            delay = t_arr - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(inst.X, inst.ybar, tol=args.tol, max_iter=max_iter))
+        for r in ids:
+            srv.wait(r, 3600)
+        polls = [srv.poll(r) for r in ids]
+        stats = srv.stats()
+    wall = time.perf_counter() - t0
+    lat = sorted(p[3] for p in polls)
+    served = {"solves_per_s": len(ids) / wall, "p50_s": lat[len(lat) // 2],
+              "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "converged": sum(p[1] == 0 for p in polls),
+              "wall_s": wall, "busy_s": stats["busy_s"]}
+    # plain single-instance path, FIFO over the same arrival times
+    clock = 0.0
+    lat_plain, conv_plain = [], 0
+    for t_arr, inst in reqs:
+        start = max(clock, t_arr)
+        s0 = time.perf_counter()
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20) as s:
+            ok, rec = s.solve(args.tol, max_iter)
+        clock = start + (time.perf_counter() - s0)
+        lat_plain.append(clock - t_arr)
+        conv_plain += int(ok)
+    lat_plain.sort()
+    plain = {"solves_per_s": len(reqs) / clock, "p50_s": lat_plain[len(lat_plain) // 2],
+             "p99_s": lat_plain[min(len(lat_plain) - 1, int(0.99 * len(lat_plain)))], "converged": conv_plain,
+             "wall_s": clock}
+    line = {"metric": "solves_per_s", "value": served["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve_poisson{args.rate:g}_{len(reqs)}req_N200-{args.N_max}_n2-32",
+                       "gamma": GAMMA, "tol": args.tol, "max_iter": max_iter, "mem_cap_GB": 60},
+            "served": served, "plain_single_instance": plain,
+            "offered_rate": args.rate, "achieved_rate": served["solves_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,8 +272,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "batch"],
-                    help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "batch", "serve"],
+                    help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances; "
+                         "serve: Poisson request stream through the serving runtime")
+    ap.add_argument("--rate", type=float, default=20.0, help="requests/s in --mode serve")
+    ap.add_argument("--N-max", type=int, default=4000, help="largest N of a request in --mode serve")
     ap.add_argument("--count", type=int, default=256, help="instances in --mode batch")
     ap.add_argument("--tol", type=float, default=1e-4)
     args = ap.parse_args()
@@ -225,6 +286,8 @@ def main():
         return run_reference(args)
     if args.mode == "batch":
         return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
 

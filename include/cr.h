@@ -212,6 +212,56 @@ CR_API cr_status cr_batch_autotune(cr_batch *b, int iters, int *tile_cols);
 
 CR_API void cr_batch_destroy(cr_batch *b);
 
+/* ------------------------------------------------------------------------------------
+ * Serving: a request queue in front of one batch, driven by a server thread.  Requests
+ * (one instance each) are admitted in arrival order while their device memory
+ * (cr_batch_instance_bytes) fits under mem_cap and fewer than max_active run; admitted
+ * instances join the running ones at the next block of opt->check_every iterations, share
+ * their launches, and retire at their own tolerance, which frees their memory for the queue.
+ * Submit/poll/wait/result may be called from any thread.
+ * ------------------------------------------------------------------------------------ */
+typedef struct cr_server cr_server;
+
+typedef struct cr_serve_stats {
+    long long completed;  /* requests finished (converged, capped or failed) */
+    long long converged;  /* finished with CR_OK */
+    long long queued;     /* waiting for admission */
+    long long running;    /* on the GPU */
+    long long mem_used;   /* device bytes reserved by running requests */
+    long long mem_cap;
+    double p50_s, p99_s;  /* submit-to-finish latency percentiles of finished requests */
+    double elapsed_s;     /* since cr_server_create */
+    double busy_s;        /* time spent in iteration blocks */
+} cr_serve_stats;
+
+/* opt as in cr_batch_create; mem_cap_bytes > 0; max_active >= 1; stream as in cr_create. */
+CR_API cr_status cr_server_create(const cr_options *opt, long long mem_cap_bytes, int max_active, void *stream,
+                                  cr_server **out);
+
+/* Queues one solve of Eq. (regularize) (inputs copied before returning; host or device).
+ * CR_ENOMEM if the instance alone exceeds the memory cap. */
+CR_API cr_status cr_server_submit(cr_server *s, const double *X, const double *ybar, long long N, int n,
+                                  double rel_gap_tol, long long max_iter, long long *req_id);
+
+/* *state: 0 queued, 1 running, 2 finished; *status: CR_OK, CR_ENOTCONV or an error (when
+ * finished); *info: last convergence record; *latency_s: submit-to-finish, or -1. */
+CR_API cr_status cr_server_poll(cr_server *s, long long req_id, int *state, int *status, cr_gap_info *info,
+                                double *latency_s);
+
+/* Blocks until the request is finished (CR_OK) or timeout_s passes (CR_ETIMEOUT). */
+CR_API cr_status cr_server_wait(cr_server *s, long long req_id, double timeout_s);
+
+/* Copies eta(lambda^k) of a finished request (y: N, xi: N x n; host or device). */
+CR_API cr_status cr_server_result(cr_server *s, long long req_id, double *y, double *xi);
+
+/* Forgets a finished request (its host result buffers are freed). */
+CR_API cr_status cr_server_release(cr_server *s, long long req_id);
+
+CR_API cr_status cr_server_stats(cr_server *s, cr_serve_stats *out);
+
+/* Stops the server thread after the current block and frees everything. */
+CR_API void cr_server_destroy(cr_server *s);
+
 CR_API const char *cr_strerror(cr_status s);
 CR_API const char *cr_last_error(void);
 CR_API int cr_version(void);

@@ -19,7 +19,7 @@ __all__ = [
     "CR_FP64", "CR_FP32", "CR_MIXED_TF32", "CR_L_HESSIAN", "CR_L_PAPER", "CR_MAX_N", "CRError",
     "default_options", "cr_create", "cr_dual_step", "cr_dual_step_timed", "cr_solve", "cr_primal",
     "cr_gap", "cr_lambda", "cr_lipschitz", "cr_iterations", "cr_describe", "cr_destroy", "Solver",
-    "library_path", "Batch", "cr_batch_instance_bytes",
+    "library_path", "Batch", "cr_batch_instance_bytes", "Server",
 ]
 
 
@@ -273,6 +273,71 @@ class Batch:
     def close(self):
         if self.handle:
             _lib().cr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (cr_server_* of include/cr.h)."""
+
+    def __init__(self, mem_cap_bytes=60 << 30, max_active=256, stream=None, **options):
+        self.opt = default_options(**options)
+        self.handle = ctypes.c_void_p()
+        check(_lib().cr_server_create(ctypes.byref(self.opt), int(mem_cap_bytes), int(max_active),
+                                      _stream_handle(stream), ctypes.byref(self.handle)))
+        self.shapes = {}
+
+    def submit(self, X, ybar, tol=1e-4, max_iter=100000):
+        xp, xk = _ptr(X)
+        yp, yk = _ptr(ybar)
+        N, n = int(xk.shape[0]), int(xk.shape[1])
+        rid = ctypes.c_longlong()
+        check(_lib().cr_server_submit(self.handle, xp, yp, N, n, float(tol), int(max_iter), ctypes.byref(rid)))
+        self.shapes[rid.value] = (N, n)
+        return rid.value
+
+    def poll(self, rid):
+        state = ctypes.c_int()
+        st = ctypes.c_int()
+        g = cr_gap_info()
+        lat = ctypes.c_double()
+        check(_lib().cr_server_poll(self.handle, int(rid), ctypes.byref(state), ctypes.byref(st), ctypes.byref(g),
+                                    ctypes.byref(lat)))
+        return int(state.value), int(st.value), g.as_dict(), float(lat.value)
+
+    def wait(self, rid, timeout=600.0):
+        check(_lib().cr_server_wait(self.handle, int(rid), float(timeout)))
+
+    def result(self, rid):
+        N, n = self.shapes[rid]
+        y = np.empty(N)
+        xi = np.empty((N, n))
+        check(_lib().cr_server_result(self.handle, int(rid), ctypes.c_void_p(y.ctypes.data),
+                                      ctypes.c_void_p(xi.ctypes.data)))
+        return y, xi
+
+    def release(self, rid):
+        check(_lib().cr_server_release(self.handle, int(rid)))
+
+    def stats(self):
+        st = _capi.cr_serve_stats()
+        check(_lib().cr_server_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            _lib().cr_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

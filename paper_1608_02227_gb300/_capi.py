@@ -48,6 +48,24 @@ class cr_gap_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class cr_serve_stats(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_longlong),
+        ("converged", ctypes.c_longlong),
+        ("queued", ctypes.c_longlong),
+        ("running", ctypes.c_longlong),
+        ("mem_used", ctypes.c_longlong),
+        ("mem_cap", ctypes.c_longlong),
+        ("p50_s", ctypes.c_double),
+        ("p99_s", ctypes.c_double),
+        ("elapsed_s", ctypes.c_double),
+        ("busy_s", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class CRError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -88,6 +106,17 @@ _SIGS = [
     ("cr_batch_instance_bytes", ctypes.c_longlong, [ctypes.c_longlong, ctypes.c_int]),
     ("cr_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("cr_batch_destroy", None, [_vp]),
+    ("cr_server_create", ctypes.c_int, [ctypes.POINTER(cr_options), ctypes.c_longlong, ctypes.c_int, _vp,
+                                        ctypes.POINTER(_vp)]),
+    ("cr_server_submit", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    ("cr_server_poll", ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(cr_gap_info), _dp]),
+    ("cr_server_wait", ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_double]),
+    ("cr_server_result", ctypes.c_int, [_vp, ctypes.c_longlong, _vp, _vp]),
+    ("cr_server_release", ctypes.c_int, [_vp, ctypes.c_longlong]),
+    ("cr_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(cr_serve_stats)]),
+    ("cr_server_destroy", None, [_vp]),
     ("cr_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("cr_last_error", ctypes.c_char_p, []),
     ("cr_version", ctypes.c_int, []),
