@@ -209,13 +209,28 @@ __global__ void __launch_bounds__(kCT) cert_combine_kernel(const CertArgs a) {
         last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
+    if (!last) return;
+    // last CTA: fixed-order parallel reduction of the per-CTA partials
+    __threadfence();
+    {
         double P = 0.0, I = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            P += ((volatile double *)a.blockpart)[b * 2 + 0];
-            I += ((volatile double *)a.blockpart)[b * 2 + 1];
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kCT) {
+            P += __ldcg(a.blockpart + b * 2 + 0);
+            I += __ldcg(a.blockpart + b * 2 + 1);
         }
+        sh[0][threadIdx.x] = P;
+        sh[1][threadIdx.x] = I;
+    }
+    __syncthreads();
+    for (int w = kCT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double P = sh[0][0], I = sh[1][0];
         st->cert_P = P;
         st->cert_infeas_sq = I;
         st->cert_counter = 0u;

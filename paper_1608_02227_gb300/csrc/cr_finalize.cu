@@ -135,14 +135,32 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         }
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
+    if (!last) return;
+    // last CTA: reduce the per-CTA partials in a fixed order (thread t takes CTAs t, t+256, ...)
+    __threadfence();
+    {
         double aa = 0.0, ay = 0.0, bb = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            aa += ((volatile double *)a.blockpart)[b * 3 + 0];
-            ay += ((volatile double *)a.blockpart)[b * 3 + 1];
-            bb += ((volatile double *)a.blockpart)[b * 3 + 2];
+        for (int b = threadIdx.x; b < nblk; b += kFX * kFY) {
+            aa += __ldcg(a.blockpart + b * 3 + 0);
+            ay += __ldcg(a.blockpart + b * 3 + 1);
+            bb += __ldcg(a.blockpart + b * 3 + 2);
         }
+        s_c[ty][tx] = aa;
+        s_u[ty][tx] = ay;
+        s_b[ty][tx] = bb;
+    }
+    __syncthreads();
+    for (int w = kFX * kFY / 2; w > 0; w >>= 1) {
+        const int t = threadIdx.x;
+        if (t < w) {
+            (&s_c[0][0])[t] += (&s_c[0][0])[t + w];
+            (&s_u[0][0])[t] += (&s_u[0][0])[t + w];
+            (&s_b[0][0])[t] += (&s_b[0][0])[t + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double aa = s_c[0][0], ay = s_u[0][0], bb = s_b[0][0];
         // g_gamma(lambda) = -1/2||a||^2 - a.ybar - ||b||^2/(2 gamma)   (Eq. g_gamma at eta(lambda))
         const double g = -0.5 * aa - ay - bb / (2.0 * gamma);
         const double rr = 0.5 * aa + bb / (2.0 * gamma);

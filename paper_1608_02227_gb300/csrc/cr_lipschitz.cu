@@ -63,19 +63,24 @@ __global__ void scatter_kernel(const double *X, int N, int n, const double *mean
     }
 }
 
-// cyclic Jacobi on the n x n symmetric Sc, one warp: every lane recomputes the rotation
-// and updates one row/column index r of A and of the accumulated vectors V (columns =
-// eigenvectors).  D (n) and V (n x n) are written at the end.
+// Jacobi eigendecomposition of the n x n symmetric Sc by one warp, parallel ordering:
+// each sweep has m-1 rounds (m = n rounded up to even) of m/2 disjoint pairs (circle
+// schedule); lane i computes the rotation of pair i, then lane r applies all rotations of
+// the round to row/column r of A and to row r of V.  D (n) and V (n x n, columns =
+// eigenvectors) are written at the end.
 __global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
     __shared__ double A[CR_MAX_N * CR_MAX_N];
     __shared__ double Q[CR_MAX_N * CR_MAX_N];
+    __shared__ double rc[CR_MAX_N / 2], rs[CR_MAX_N / 2];
+    __shared__ int rp[CR_MAX_N / 2], rq[CR_MAX_N / 2];
     const int lane = threadIdx.x;
+    const int m = (n + 1) & ~1;
     for (int i = lane; i < n * n; i += 32) {
         A[i] = Sc[i];
         Q[i] = (i / n == i % n) ? 1.0 : 0.0;
     }
     __syncwarp();
-    for (int sweep = 0; sweep < 100; ++sweep) {
+    for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0, dia = 0.0;
         for (int i = lane; i < n * n; i += 32) {
             const int p = i / n, q = i % n;
@@ -89,30 +94,54 @@ __global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
             dia += __shfl_xor_sync(0xffffffffu, dia, o);
         }
         if (off <= 1e-32 * dia || off == 0.0) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
-                if (apq == 0.0) continue;
-                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                __syncwarp();
-                if (lane < n) {  // A <- A J (columns p, q)
-                    const double arp = A[lane * n + p], arq = A[lane * n + q];
-                    A[lane * n + p] = c * arp - s * arq;
-                    A[lane * n + q] = s * arp + c * arq;
-                    const double qrp = Q[lane * n + p], qrq = Q[lane * n + q];
-                    Q[lane * n + p] = c * qrp - s * qrq;
-                    Q[lane * n + q] = s * qrp + c * qrq;
+        for (int round = 0; round < m - 1; ++round) {
+            if (lane < m / 2) {
+                // circle method: position 0 fixed, the others rotate by `round`
+                const int a0 = lane == 0 ? 0 : ((lane - 1 + round) % (m - 1)) + 1;
+                const int b0 = ((m - 1 - lane - 1 + round) % (m - 1)) + 1;
+                const int p = min(a0, b0), q = max(a0, b0);
+                double c = 1.0, sn = 0.0;
+                if (q < n) {
+                    const double apq = A[p * n + q];
+                    if (apq != 0.0) {
+                        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sn = t * c;
+                    }
                 }
-                __syncwarp();
-                if (lane < n) {  // A <- J^T A (rows p, q)
-                    const double apr = A[p * n + lane], aqr = A[q * n + lane];
-                    A[p * n + lane] = c * apr - s * aqr;
-                    A[q * n + lane] = s * apr + c * aqr;
-                }
-                __syncwarp();
+                rp[lane] = p;
+                rq[lane] = q;
+                rc[lane] = c;
+                rs[lane] = sn;
             }
+            __syncwarp();
+            if (lane < n) {  // A <- A J and V <- V J: row `lane`, all pairs of the round
+                for (int i = 0; i < m / 2; ++i) {
+                    const int p = rp[i], q = rq[i];
+                    if (q >= n || rs[i] == 0.0) continue;
+                    const double c = rc[i], sn = rs[i];
+                    const double arp = A[lane * n + p], arq = A[lane * n + q];
+                    A[lane * n + p] = c * arp - sn * arq;
+                    A[lane * n + q] = sn * arp + c * arq;
+                    const double qrp = Q[lane * n + p], qrq = Q[lane * n + q];
+                    Q[lane * n + p] = c * qrp - sn * qrq;
+                    Q[lane * n + q] = sn * qrp + c * qrq;
+                }
+            }
+            __syncwarp();
+            if (lane < n) {  // A <- J^T A: column `lane`, all pairs of the round
+                for (int i = 0; i < m / 2; ++i) {
+                    const int p = rp[i], q = rq[i];
+                    if (q >= n || rs[i] == 0.0) continue;
+                    const double c = rc[i], sn = rs[i];
+                    const double apr = A[p * n + lane], aqr = A[q * n + lane];
+                    A[p * n + lane] = c * apr - sn * aqr;
+                    A[q * n + lane] = sn * apr + c * aqr;
+                }
+            }
+            __syncwarp();
+        }
     }
     for (int i = lane; i < n; i += 32) D[i] = A[i * n + i];
     for (int i = lane; i < n * n; i += 32) V[i] = Q[i];
@@ -143,7 +172,51 @@ __global__ void secular_kernel(const double *X, int N, int n, const double *mean
         }
         double lo = Dm, hi = Dm + (double)N * ee;
         if (ee > 0.0) {
-            for (int it = 0; it < 400; ++it) {
+            // f(mu) = 1 - N sum e_k^2 / (mu - D_k) is increasing and concave on (max D, inf);
+            // 16 bisection steps, then Newton from the left end (monotone towards the root)
+            for (int it = 0; it < 16; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                double f = 1.0;
+                for (int k = 0; k < n; ++k) f -= (double)N * e[k] * e[k] / (mid - sD[k]);
+                if (f < 0.0)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            double mu_n = lo;
+            for (int it = 0; it < 40 && mu_n > Dm; ++it) {
+                double f = 1.0, fp = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const double w = 1.0 / (mu_n - sD[k]);
+                    const double t = (double)N * e[k] * e[k] * w;
+                    f -= t;
+                    fp += t * w;
+                }
+                if (f >= 0.0) {  // at or right of the root: an upper bound
+                    hi = fmin(hi, mu_n);
+                    break;
+                }
+                lo = mu_n;
+                const double next = mu_n - f / fp;
+                if (!(next > mu_n) || next >= hi) break;
+                if (next - mu_n <= 1e-16 * next) {
+                    mu_n = next;
+                    continue;
+                }
+                mu_n = next;
+            }
+            // Newton approached the root from below: try a right end just above it
+            {
+                const double cand = lo + fmax(8e-16 * fabs(lo), 1e-300);
+                if (cand < hi) {
+                    double f = 1.0;
+                    for (int k = 0; k < n; ++k) f -= (double)N * e[k] * e[k] / (cand - sD[k]);
+                    if (f >= 0.0) hi = cand;
+                }
+            }
+            // finish with bisection on the (now tiny) bracket; hi is kept, never underestimating
+            for (int it = 0; it < 200; ++it) {
                 const double mid = 0.5 * (lo + hi);
                 if (mid <= lo || mid >= hi) break;
                 double f = 1.0;
