@@ -83,6 +83,23 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.rowpart = (double *)c->rowpart;
         a.colpart = (double *)c->colpart;
         CR_CUDA(launch_sweep_d(c->NP, a, c->grid, c->stream));
+    } else if (c->tc) {
+        TcSweepArgs a{};
+        a.ld = c->ld;
+        a.N = c->N;
+        a.n = c->n;
+        a.NP = c->NP;
+        a.row_blocks = c->RB;
+        a.col_splits = c->S;
+        a.cols_per_split = c->cps;
+        a.st = c->st;
+        a.rowpart = (float *)c->rowpart;
+        a.colpart = (float *)c->colpart;
+        a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
+        TcMaps m = c->tcm;
+        m.P = &c->tc_lam[P];
+        m.Q = &c->tc_lam[Q];
+        CR_CUDA(launch_sweep_tc(m, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
         a.Q = (float *)c->lam[Q];
@@ -147,6 +164,7 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
     f.u64 = c->u64;
     f.xiT64 = c->xiT64;
     f.xT32 = c->xT32;
+    f.xi_rm = c->xi_rm;
     f.blockpart = c->finblk;
     f.log = c->log;
     f.st = c->st;
@@ -221,10 +239,13 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     // FP32 runs the TMA-pipelined sweep; CR_SWEEP=simple selects the plain FP32 kernel
     // (same arithmetic, loads through registers) for A/B measurements.
     const char *variant = getenv("CR_SWEEP");
-    c->tma = !f64 && !(variant && strcmp(variant, "simple") == 0);
-    c->rows = c->tma ? sweep_tma_rows(c->NP) : cfg.rows;
+    c->tc = c->opt.precision == CR_MIXED_TF32;
+    c->tma = !f64 && !c->tc && !(variant && strcmp(variant, "simple") == 0);
+    c->rows = c->tc ? sweep_tc_rows() : (c->tma ? sweep_tma_rows(c->NP) : cfg.rows);
     c->RB = (N + c->rows - 1) / c->rows;
-    if (c->tma)
+    if (c->tc)
+        CR_CUDA(sweep_tc_occupancy(&c->occ));
+    else if (c->tma)
         CR_CUDA(sweep_tma_occupancy(c->NP, &c->occ));
     else
         CR_CUDA(f64 ? sweep_occupancy_d(c->NP, &c->occ) : sweep_occupancy_f(c->NP, &c->occ));
@@ -317,6 +338,24 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(cudaMemsetAsync(c->ha[i], 0, sizeof(double) * N, c->stream));
         CR_CUDA(cudaMemsetAsync(c->hb[i], 0, sizeof(double) * N * n, c->stream));
     }
+    if (c->tc) {
+        const size_t rm = (size_t)c->ldv * 32;
+        CR_TRY(dev_alloc(c, &c->xr, 2 * rm));
+        CR_TRY(dev_alloc(c, &c->xt, 2 * rm));
+        CR_TRY(dev_alloc(c, &c->xi_rm, 2 * rm));
+        CR_CUDA(cudaMemsetAsync(c->xi_rm, 0, 2 * rm * sizeof(float), c->stream));
+        CR_CUDA(launch_tc_points(c->X, N, n, c->ldv, c->xr, c->xt, c->stream));
+        for (int i = 0; i < 2; ++i)
+            CR_CUDA(make_tmap_2d(&c->tc_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 32, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 32, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XTh, c->xt, c->ldv, 32, c->ldv, 32, 32, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XTl, c->xt + rm, c->ldv, 32, c->ldv, 32, 32, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.Y, c->yh, c->ldv, 2, c->ldv, 32, 2));
+        CR_CUDA(make_tmap_2d(&c->tcm.XIh, c->xi_rm, 32, c->ldv, 32, 32, 128, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XIl, c->xi_rm + rm, 32, c->ldv, 32, 32, 128, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.U, c->uh, c->ldv, 2, c->ldv, 128, 2));
+    }
     if (c->tma) {
         for (int i = 0; i < 2; ++i)
             CR_CUDA(make_tmap_2d(&c->tm_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, kChunk, c->rows));
@@ -387,6 +426,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     f.u64 = c->u64;
     f.xiT64 = c->xiT64;
     f.xT32 = c->xT32;
+    f.xi_rm = c->xi_rm;
     f.blockpart = c->finblk;
     f.log = c->log;
     f.st = c->st;
@@ -512,8 +552,8 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
         set_err("unknown precision %d", o.precision);
         return CR_EINVAL;
     }
-    if (o.precision == CR_MIXED_TF32) {
-        set_err("CR_MIXED_TF32 is not built into this library");
+    if (o.precision == CR_MIXED_TF32 && n > 31) {
+        set_err("CR_MIXED_TF32 handles n <= 31 (a row of ones joins the 32-wide operand)");
         return CR_EUNSUPPORTED;
     }
     if (!(o.lipschitz >= 0.0) || !isfinite(o.lipschitz)) {
@@ -736,7 +776,7 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              "\"sweep\": \"%s\"}",
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
              pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters,
-             c->tma ? "tma" : (is_f64(c) ? "fp64" : "simple"));
+             c->tc ? "tcgen05" : (c->tma ? "tma" : (is_f64(c) ? "fp64" : "simple")));
     return CR_OK;
 }
 

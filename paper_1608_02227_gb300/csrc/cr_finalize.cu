@@ -48,8 +48,10 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
             PT v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = colp[(long long)(b + u * kFY) * a.ld + l];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) c += (double)v[u];
+            // FP32 partials: pairwise sums of 8 in FP32 (error ~3 ulp of the group, the level
+            // of the FP32 multipliers themselves), groups accumulated in FP64; GB300's FP64
+            // pipe is the limit of this kernel otherwise.  FP64 partials stay FP64 throughout.
+            c += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
         }
         for (; b < a.row_blocks; b += kFY) c += (double)colp[(long long)b * a.ld + l];
     }
@@ -87,6 +89,10 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
                 // the sweep sees the rounded xi and x; u is formed from exactly those
                 const float xf = (float)xi;
                 a.xiT[(long long)k * a.ldv + l] = xf;
+                if (a.xi_rm) {  // tensor-core operand: hi = xf (read as trunc(xf)), lo = xf - trunc(xf)
+                    a.xi_rm[(long long)l * 32 + k] = xf;
+                    a.xi_rm[a.ldv * 32 + (long long)l * 32 + k] = xf - __uint_as_float(__float_as_uint(xf) & 0xFFFFE000u);
+                }
                 upart -= (double)xf * (double)a.xT32[(long long)k * a.ldv + l];
             }
         }
@@ -244,6 +250,23 @@ __global__ void transpose_points_kernel(const double *X, int N, int n, int NP, l
     }
 }
 
+__global__ void tc_points_kernel(const double *X, int N, int n, long long ldv, float *xr, float *xt) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= ldv * 32) return;
+    const long long j = q / 32;
+    const int k = (int)(q - j * 32);
+    float hi = 0.f, lo = 0.f, one = 0.f;
+    if (j < N && k < n) {
+        hi = (float)X[j * n + k];
+        lo = hi - __uint_as_float(__float_as_uint(hi) & 0xFFFFE000u);
+    }
+    if (j < N && k == n) one = 1.f;
+    xr[j * 32 + k] = hi;
+    xr[ldv * 32 + j * 32 + k] = lo;
+    xt[(long long)k * ldv + j] = (k == n) ? one : hi;
+    xt[32 * ldv + (long long)k * ldv + j] = lo;
+}
+
 __global__ void lambda_to_f64_kernel(const void *lam, int is_f32, int N, long long ld, long long row0,
                                      long long rows, double *out, long long ldo) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -298,6 +321,11 @@ cudaError_t launch_lambda_to_f64(const void *lam, int is_f32, int N, long long l
     if (rows <= 0) return cudaSuccess;
     lambda_to_f64_kernel<<<blocks_for(rows * N, 256), 256, 0, s>>>(lam, is_f32, N, ld, row0, rows, out,
                                                                    ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_points(const double *X, int N, int n, long long ldv, float *xr, float *xt, cudaStream_t s) {
+    tc_points_kernel<<<blocks_for(ldv * 32, 256), 256, 0, s>>>(X, N, n, ldv, xr, xt);
     return cudaGetLastError();
 }
 

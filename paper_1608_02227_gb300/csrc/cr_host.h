@@ -44,6 +44,10 @@ struct cr_ctx {
     bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
     CUtensorMap tm_lam[2];
     TmaMaps tm{};
+    bool tc = false;             // CR_MIXED_TF32: tensor-core sweep (cr_sweep_tc.cu)
+    CUtensorMap tc_lam[2];
+    TcMaps tcm{};
+    float *xr = nullptr, *xt = nullptr, *xi_rm = nullptr;
     // graph of graph_iters iterations starting at an even k
     cudaGraphExec_t gexec = nullptr;
     int glen = 0;

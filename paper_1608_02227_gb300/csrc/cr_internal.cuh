@@ -123,7 +123,32 @@ cudaError_t sweep_tma_occupancy(int np, int *blocks_per_sm);
 int sweep_tma_rows(int np);
 void sweep_tma_diag(int *v4);  // regs, max threads, smem, threads of a kernel that did not fit   // rows per work item of the TMA sweep for bucket np
 cudaError_t make_tmap_2d(CUtensorMap *tm, const float *base, long long cols, long long rows, long long ld,
-                         int box_cols, int box_rows);
+                         int box_cols, int box_rows, bool swizzle128 = false);
+
+// Tensor-core sweep (cr_sweep_tc.cu, CR_MIXED_TF32): 128-row items, 32-column chunks
+struct TcSweepArgs {
+    long long ld;
+    int N, n, NP;
+    int row_blocks, col_splits, cols_per_split;
+    const DevState *st;
+    float *rowpart;          // S x N x (NP+1)
+    float *colpart;          // RB x ld (128-row blocks)
+    int *err;
+};
+struct TcMaps {
+    const CUtensorMap *P, *Q;            // lambda buffers [N][ld], box 32 x 128, 128-byte swizzle
+    CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 32, swizzle
+    CUtensorMap XTh, XTl;                // points transposed + ones row [32][ldv], box 32 x 32, swizzle
+    CUtensorMap Y;                       // y hi / lo [2][ldv], box 32 x 2
+    CUtensorMap XIh, XIl;                // xi row-major [ldv][32] hi / lo, box 32 x 128, swizzle
+    CUtensorMap U;                       // u hi / lo [2][ldv], box 128 x 2
+};
+cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cudaStream_t s);
+cudaError_t sweep_tc_occupancy(int *blocks_per_sm);
+int sweep_tc_rows();
+// points for the tensor-core sweep: xr [2][ldv][32] (hi = x as FP32, lo = x - trunc(x)),
+// xt [2][32][ldv] (transposed, with a row of ones at index n in the hi half)
+cudaError_t launch_tc_points(const double *X, int N, int n, long long ldv, float *xr, float *xt, cudaStream_t s);
 
 // Batched sweep: one descriptor per instance (device memory, tensor maps included) and a
 // work-list of items; the P/Q parity of an instance is its device counter k modulo 2.
@@ -168,6 +193,7 @@ struct FinArgs {
     float *yh, *yl, *uh, *ul, *xiT;      // FP32 mode
     double *y64, *u64, *xiT64;           // FP64 mode
     const float *xT32;                   // FP32 points (u uses the rounded xi and x)
+    float *xi_rm;                        // tensor-core sweep: xi row-major [2][ldv][32] (hi, lo), or NULL
     double *blockpart;       // gridDim x 3
     double *log;             // kLogCap x 3
     DevState *st;

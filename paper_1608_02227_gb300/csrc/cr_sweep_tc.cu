@@ -1,0 +1,507 @@
+// cr_sweep_tc.cu -- the Lambda sweep with both contractions on the tensor cores
+// (CR_MIXED_TF32): Steps 2 and 4 of Figure "papg" (K = N) and the C^T reductions, with
+//     S   = Xi_blk . X_chunk^T      (rho_ij = u_i - y_j + S_ij)          [GEMM1]
+//     ACC += Lambda_blk . [X | 1]_chunk  (row sums of Lambda.X and of Lambda) [GEMM2]
+// as tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory.  TF32 keeps the top
+// 19 bits of each FP32 operand (the hardware truncates), so every operand v is split into
+// hi = v (read as trunc(v)) and lo = v - trunc(v), and each product is formed as
+// hi.hi + hi.lo + lo.hi: close to FP32 accuracy.
+//
+// CTA = 6 warps, one CTA per SM, work items of 128 rows x one column split, walked in
+// chunks of 32 columns:
+//   warp 0  producer: 2-D TMA loads (128-byte swizzle) of the lambda^{k-1}, lambda^{k-2}
+//           tiles (128 x 32), the chunk's x rows (hi, lo; 32 x 32), its transposed x with a
+//           row of ones (hi, lo; 32 x 32) and y (hi, lo); per item the xi rows (hi, lo;
+//           128 x 32) and u (hi, lo) -- into a ring of stages guarded by mbarriers;
+//   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 of chunk c+1
+//           is issued before GEMM2 of chunk c, so the epilogue of c overlaps the MMAs;
+//   warps 2-5  epilogue, thread = row (tensor-memory lane): reads S from tensor memory,
+//           forms lambda^k, writes it over the consumed lambda^{k-1} tile (it is the A
+//           operand of GEMM2 and the source of the TMA store of lambda^k) and its low part
+//           over the lambda^{k-2} tile, reduces column sums with warp shuffles, and at the
+//           end of an item reads the GEMM2 accumulator (row partials).
+// Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "cr_internal.cuh"
+
+namespace cr {
+namespace {
+
+constexpr int kM = 128;       // rows per item (MMA M, tensor-memory lanes)
+constexpr int kC = 32;        // columns per chunk (GEMM1 N, GEMM2 K)
+constexpr int kK = 32;        // GEMM1 K (point dimension padded) and GEMM2 N
+constexpr int kStages = 3;
+constexpr int kTiles = kM * kC * 4;             // bytes of one 128 x 32 FP32 tile (16 KB)
+constexpr int kSmall = kC * kK * 4;             // bytes of one 32 x 32 FP32 tile (4 KB)
+// stage layout (bytes): P | Q | XRh | XRl | XTh | XTl | Y(hi 32, lo 32) | colx[4][32] | pad
+constexpr int kOffP = 0, kOffQ = kTiles, kOffXRh = 2 * kTiles, kOffXRl = kOffXRh + kSmall;
+constexpr int kOffXTh = kOffXRl + kSmall, kOffXTl = kOffXTh + kSmall, kOffY = kOffXTl + kSmall;
+constexpr int kOffColx = kOffY + 2 * kC * 4;
+constexpr int kStageBytes = ((kOffColx + 4 * kC * 4 + 1023) / 1024) * 1024;
+constexpr int kTxStage = 2 * kTiles + 4 * kSmall + 2 * kC * 4;
+// item buffer: XIh | XIl | U(hi 128, lo 128)
+constexpr int kItemBytes = ((2 * kTiles + 2 * kM * 4 + 1023) / 1024) * 1024;
+constexpr int kTxItem = 2 * kTiles + 2 * kM * 4;
+constexpr int kThreads = 6 * 32;
+constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kItemBytes + 512;
+constexpr uint32_t kTmemCols = 128;             // S[2] (2 x 32) + ACC[2] (2 x 32)
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t ph) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(ph)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on the phase `use` of a barrier (completes when the barrier has finished
+// phase number `use`); false when the CTA aborts
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t use, volatile int *abort_flag, int *err) {
+    const uint32_t ph = use & 1u;
+    if (bar_try(b, ph)) return true;
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        if (bar_try(b, ph)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicExch(err, CR_ETIMEOUT);
+            return false;
+        }
+    }
+}
+// wait for the release of the previous use of a slot (first use passes at once)
+__device__ __forceinline__ bool slot_wait(uint64_t *b, uint32_t use, volatile int *abort_flag, int *err) {
+    return use == 0 ? true : bar_wait(b, use - 1, abort_flag, err);
+}
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store(const CUtensorMap *tm, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(su32(src)), "r"(x), "r"(y)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand in a 128-byte-swizzled tile: rows of 128 B, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+// kind::tf32, D = F32, A and B TF32 K-major, M = 128, N = 32
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"((uint32_t)acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+// D (+)= sum over (A_hi, B_hi), (A_hi, B_lo), (A_lo, B_hi) of A . B^T, K = 32 in 4 steps
+__device__ __forceinline__ void gemm3(uint32_t tmem_d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                      bool acc_first) {
+    const uint32_t A[3] = {ah, ah, al}, B[3] = {bh, bl, bh};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int k = 0; k < kK / 8; ++k)
+            mma(tmem_d, sdesc(A[p] + 32 * k), sdesc(B[p] + 32 * k), acc_first || p > 0 || k > 0);
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_lo(float v) { return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+struct Item {
+    int rb, sp, i0;
+    long long c0, c1;
+    int nch;
+};
+__device__ __forceinline__ Item item_of(const TcSweepArgs &a, int item) {
+    Item it;
+    it.rb = item / a.col_splits;
+    it.sp = item - it.rb * a.col_splits;
+    it.i0 = it.rb * kM;
+    it.c0 = (long long)it.sp * a.cols_per_split;
+    it.c1 = min(it.c0 + (long long)a.cols_per_split, a.ld);
+    it.nch = (int)((it.c1 - it.c0 + kC - 1) / kC);
+    return it;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sweep_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
+                    const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
+                    const __grid_constant__ CUtensorMap tmXTh, const __grid_constant__ CUtensorMap tmXTl,
+                    const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmXIh,
+                    const __grid_constant__ CUtensorMap tmXIl, const __grid_constant__ CUtensorMap tmU,
+                    const TcSweepArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *stage0 = base;
+    unsigned char *item0 = base + (size_t)kStages * kStageBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(item0 + 2 * (size_t)kItemBytes);
+    uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
+    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + lambda^k tile stored (2 arrivals)
+    uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
+    uint64_t *sfull = lamr + kStages;       // [2] GEMM1 result in S[b]
+    uint64_t *sempty = sfull + 2;           // [2] S[b] read by the epilogue (4 arrivals)
+    uint64_t *xfull = sempty + 2;           // [2] xi rows of an item landed
+    uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item done + u read (5 arrivals)
+    uint64_t *afull = xempty + 2;           // [2] accumulator of an item complete
+    uint64_t *aempty = afull + 2;           // [2] accumulator read (4 arrivals)
+    uint64_t *fin = aempty + 2;             // all MMAs done (teardown)
+    int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
+    volatile int *abort_flag = ticket + kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int items = a.row_blocks * a.col_splits;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 2);
+            bar_init(&lamr[s], 4);
+            ticket[s] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&sfull[b], 1);
+            bar_init(&sempty[b], 4);
+            bar_init(&xfull[b], 1);
+            bar_init(&xempty[b], 5);
+            bar_init(&afull[b], 1);
+            bar_init(&aempty[b], 4);
+        }
+        bar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tS[2] = {tmem, tmem + 32}, tA[2] = {tmem + 64, tmem + 96};
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t fill = 0, itn = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
+                const Item it = item_of(a, item);
+                const int xb = itn & 1;
+                unsigned char *ib = item0 + (size_t)xb * kItemBytes;
+                if (!slot_wait(&xempty[xb], itn >> 1, abort_flag, a.err)) break;
+                bar_expect(&xfull[xb], kTxItem);
+                tma_load(ib, &tmXIh, &xfull[xb], 0, it.i0);
+                tma_load(ib + kTiles, &tmXIl, &xfull[xb], 0, it.i0);
+                tma_load(ib + 2 * kTiles, &tmU, &xfull[xb], it.i0, 0);
+                for (int c = 0; c < it.nch; ++c, ++fill) {
+                    const int s = fill % kStages;
+                    const int j0 = (int)(it.c0 + (long long)c * kC);
+                    if (!slot_wait(&empty[s], fill / kStages, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = stage0 + (size_t)s * kStageBytes;
+                    bar_expect(&full[s], kTxStage);
+                    tma_load(st + kOffP, &tmP, &full[s], j0, it.i0);
+                    tma_load(st + kOffQ, &tmQ, &full[s], j0, it.i0);
+                    tma_load(st + kOffXRh, &tmXRh, &full[s], 0, j0);
+                    tma_load(st + kOffXRl, &tmXRl, &full[s], 0, j0);
+                    tma_load(st + kOffXTh, &tmXTh, &full[s], j0, 0);
+                    tma_load(st + kOffXTl, &tmXTl, &full[s], j0, 0);
+                    tma_load(st + kOffY, &tmY, &full[s], j0, 0);
+                }
+            }
+            // drain the copies still in flight before the CTA can exit
+            for (uint32_t f = fill > (uint32_t)kStages ? fill - kStages : 0; f < fill; ++f) {
+                const uint64_t t0 = gtimer();
+                while (!bar_try(&full[f % kStages], (f / kStages) & 1u) && gtimer() - t0 < 200000000ull) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            // flattened (item, chunk) sequence of this CTA; GEMM1(f+1) is issued before GEMM2(f)
+            uint32_t fill = 0, itn = 0;
+            bool ok = true;
+            // GEMM1 state: next fill to issue
+            int g1_item = blockIdx.x, g1_c = 0;
+            uint32_t g1_fill = 0, g1_itn = 0;
+            auto issue_gemm1 = [&](void) -> bool {
+                // advance to a valid (item, chunk)
+                while (g1_item < items) {
+                    const Item it = item_of(a, g1_item);
+                    if (g1_c < it.nch) break;
+                    g1_item += gridDim.x;
+                    g1_c = 0;
+                    ++g1_itn;
+                }
+                if (g1_item >= items) return true;
+                const Item it = item_of(a, g1_item);
+                const int s = g1_fill % kStages, b = g1_fill & 1, xb = g1_itn & 1;
+                if (!bar_wait(&full[s], g1_fill / kStages, abort_flag, a.err)) return false;
+                if (g1_c == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, a.err)) return false;
+                if (!slot_wait(&sempty[b], g1_fill >> 1, abort_flag, a.err)) return false;
+                tc_fence_after();
+                const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
+                const uint32_t ib = su32(item0 + (size_t)xb * kItemBytes);
+                gemm3(tS[b], ib, ib + kTiles, st + kOffXRh, st + kOffXRl, false);
+                mma_commit(&sfull[b]);
+                if (g1_c == it.nch - 1) mma_commit(&xempty[xb]);
+                ++g1_c;
+                ++g1_fill;
+                return true;
+            };
+            ok = issue_gemm1();
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
+                const Item it = item_of(a, item);
+                const int ab = itn & 1;
+                for (int c = 0; c < it.nch && ok; ++c, ++fill) {
+                    ok = issue_gemm1();  // GEMM1 of the next chunk (if any)
+                    if (!ok) break;
+                    const int s = fill % kStages;
+                    if (!bar_wait(&lamr[s], fill / kStages, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    if (c == 0 && !slot_wait(&aempty[ab], itn >> 1, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
+                    gemm3(tA[ab], st + kOffP, st + kOffQ, st + kOffXTh, st + kOffXTl, c > 0);
+                    mma_commit(&empty[s]);
+                    if (c == it.nch - 1) mma_commit(&afull[ab]);
+                }
+            }
+            mma_commit(fin);
+            const uint64_t t0 = gtimer();
+            while (!bar_try(fin, 0) && gtimer() - t0 < 500000000ull) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int r = 32 * q + lane;            // row within the item
+        const float beta = (float)a.st->beta, sstep = (float)a.st->s;
+        uint32_t fill = 0, itn = 0;
+        for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
+            const Item it = item_of(a, item);
+            const int xb = itn & 1, ab = itn & 1;
+            const int i = it.i0 + r;
+            const bool rv = i < a.N;
+            const unsigned char *ib = item0 + (size_t)xb * kItemBytes;
+            float uh = 0.f, ul = 0.f;
+            bool ok = __all_sync(0xffffffffu, bar_wait(&xfull[xb], itn >> 1, abort_flag, a.err));
+            if (ok) {
+                const float *U = reinterpret_cast<const float *>(ib + 2 * kTiles);
+                uh = U[r];
+                ul = U[kM + r];
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(&xempty[xb]);  // the item buffer may be refilled once GEMM1 is done too
+            for (int c = 0; c < it.nch; ++c, ++fill) {
+                const int s = fill % kStages, b = fill & 1;
+                const long long j0 = it.c0 + (long long)c * kC;
+                unsigned char *st = stage0 + (size_t)s * kStageBytes;
+                ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, a.err);
+                ok = ok && bar_wait(&sfull[b], fill >> 1, abort_flag, a.err);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+                float lam[32];
+                tc_fence_after();
+                if (ok) tmem_ld32(tS[b] + ((uint32_t)(32 * q) << 16), lam);  // S row r
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(&sempty[b]);
+                if (ok) {
+                    const float *Y = reinterpret_cast<const float *>(st + kOffY);
+                    float *P = reinterpret_cast<float *>(st + kOffP);
+                    float *Qs = reinterpret_cast<float *>(st + kOffQ);
+                    const int rx = r & 7;
+                    const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > a.N) ||
+                                      (it.i0 + kM > a.N);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {  // 16-byte chunk g of the row, swizzled position g ^ (r % 8)
+                        const int off = r * 32 + ((g ^ rx) << 2);
+                        const float4 p4 = *reinterpret_cast<const float4 *>(P + off);
+                        const float4 q4 = *reinterpret_cast<const float4 *>(Qs + off);
+                        const float4 yh = *reinterpret_cast<const float4 *>(Y + 4 * g);
+                        const float4 yl = *reinterpret_cast<const float4 *>(Y + kC + 4 * g);
+                        const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, qv[4] = {q4.x, q4.y, q4.z, q4.w};
+                        const float yhv[4] = {yh.x, yh.y, yh.z, yh.w}, ylv[4] = {yl.x, yl.y, yl.z, yl.w};
+                        float l4[4], lo4[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float rho = ((uh - yhv[e]) + (ul - ylv[e])) + lam[4 * g + e];
+                            const float lt = fmaf(beta, pv[e] - qv[e], pv[e]);
+                            float l = fmaxf(0.f, fmaf(sstep, rho, lt));
+                            if (edge) {
+                                const long long j = j0 + 4 * g + e;
+                                if (!rv || j >= a.N || j == i) l = 0.f;
+                            }
+                            l4[e] = l;
+                            lo4[e] = tf32_lo(l);
+                            lam[4 * g + e] = l;
+                        }
+                        *reinterpret_cast<float4 *>(P + off) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+                        *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo4[0], lo4[1], lo4[2], lo4[3]);
+                    }
+                    fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
+                    // column sums over this warp's 32 rows: transpose-reduce, lane c ends with column c
+#pragma unroll
+                    for (int w = 16; w >= 1; w >>= 1) {
+                        const bool upper = (lane & w) != 0;
+#pragma unroll
+                        for (int e = 0; e < w; ++e) {
+                            const float send = upper ? lam[e] : lam[e + w];
+                            const float keep = upper ? lam[e + w] : lam[e];
+                            lam[e] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                        }
+                    }
+                    // after the halving steps lam[0] of lane c is column c summed over the 32 rows
+                    float *colx = reinterpret_cast<float *>(st + kOffColx);
+                    colx[q * kC + lane] = lam[0];
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(&lamr[s]);
+                // last warp through: column partials (warp order) and the TMA store of lambda^k
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    last = (atomicAdd(&ticket[s], 1) == 3);
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                __syncwarp();
+                if (last) {
+                    __threadfence_block();
+                    if (ok && !*abort_flag) {
+                        const float *colx = reinterpret_cast<const float *>(st + kOffColx);
+                        const float v = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
+                        const long long j = j0 + lane;
+                        if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = v;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        ticket[s] = 0;
+                        if (ok && !*abort_flag) {
+                            tma_store(&tmQ, st + kOffP, (int)j0, it.i0);
+                            tma_store_wait_read();
+                        }
+                        bar_arrive(&empty[s]);
+                    }
+                }
+            }
+            // end of item: row partials from the GEMM2 accumulator (columns k < n: sum_j lambda_ij x_jk,
+            // column n: sum_j lambda_ij)
+            const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, a.err));
+            float acc[32];
+            tc_fence_after();
+            if (ok2) tmem_ld32(tA[ab] + ((uint32_t)(32 * q) << 16), acc);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&aempty[ab]);
+            if (ok2 && rv) {
+                float *dst = a.rowpart + ((long long)it.sp * a.N + i) * (a.NP + 1);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    if (k < a.n) dst[k] = acc[k];
+                    if (k == a.n) dst[a.NP] = acc[k];
+                }
+            }
+        }
+        tma_store_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+size_t sweep_tc_smem() { return kSmem; }
+int sweep_tc_rows() { return kM; }
+
+cudaError_t sweep_tc_occupancy(int *blocks_per_sm) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep_tc_kernel, kThreads, kSmem);
+}
+
+cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cudaStream_t s) {
+    int occ = 0;
+    cudaError_t e = sweep_tc_occupancy(&occ);
+    if (e != cudaSuccess) return e;
+    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, m.XRh, m.XRl, m.XTh, m.XTl, m.Y, m.XIh, m.XIl, m.U, a);
+    return cudaGetLastError();
+}
+
+}  // namespace cr
