@@ -7,7 +7,7 @@
 // hi = v (read as trunc(v)) and lo = v - trunc(v), and each product is formed as
 // hi.hi + hi.lo + lo.hi: close to FP32 accuracy.
 //
-// CTA = 6 warps, one CTA per SM, work items of 128 rows x one column split, walked in
+// CTA = 10 warps, one CTA per SM, work items of 128 rows x one column split, walked in
 // chunks of 32 columns:
 //   warp 0  producer: 2-D TMA loads (128-byte swizzle) of the lambda^{k-1}, lambda^{k-2}
 //           tiles (128 x 32), the chunk's x rows (hi, lo; 32 x 32), its transposed x with a
@@ -15,11 +15,13 @@
 //           128 x 32) and u (hi, lo) -- into a ring of stages guarded by mbarriers;
 //   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 of chunk c+1
 //           is issued before GEMM2 of chunk c, so the epilogue of c overlaps the MMAs;
-//   warps 2-5  epilogue, thread = row (tensor-memory lane): reads S from tensor memory,
-//           forms lambda^k, writes it over the consumed lambda^{k-1} tile (it is the A
-//           operand of GEMM2 and the source of the TMA store of lambda^k) and its low part
-//           over the lambda^{k-2} tile, reduces column sums with warp shuffles, and at the
-//           end of an item reads the GEMM2 accumulator (row partials).
+//   warps 2-9  epilogue in two groups of four that take alternate chunks (two chunks in
+//           flight), thread = row (tensor-memory lane): reads S from tensor memory, forms
+//           lambda^k (packed FP32x2 arithmetic), writes it over the consumed lambda^{k-1}
+//           tile (it is the A operand of GEMM2 and the source of the TMA store of lambda^k)
+//           and its low part over the lambda^{k-2} tile, sums its 32 x 32 block of the new
+//           tile by columns, and at the end of an item reads half of the GEMM2 accumulator
+//           (row partials).
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -44,10 +46,13 @@ constexpr int kTxStage = 2 * kTiles + 4 * kSmall + 2 * kC * 4;
 // item buffer: XIh | XIl | U(hi 128, lo 128)
 constexpr int kItemBytes = ((2 * kTiles + 2 * kM * 4 + 1023) / 1024) * 1024;
 constexpr int kTxItem = 2 * kTiles + 2 * kM * 4;
-constexpr int kThreads = 6 * 32;
+constexpr int kEpiWarps = 8;                  // two groups of four (one warp per lane quarter)
+constexpr int kHalf = kC / 2;                   // accumulator columns read by each group
+constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kItemBytes + 512;
 constexpr uint32_t kTmemCols = 128;             // S[2] (2 x 32) + ACC[2] (2 x 32)
 constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -67,9 +72,9 @@ __device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
 __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t ph) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(su32(b)), "r"(ph)
+        : "r"(su32(b)), "r"(ph), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -162,6 +167,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ float tf32_lo(float v) { return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 struct Item {
@@ -178,6 +194,50 @@ __device__ __forceinline__ Item item_of(const TcSweepArgs &a, int item) {
     it.c1 = min(it.c0 + (long long)a.cols_per_split, a.ld);
     it.nch = (int)((it.c1 - it.c0 + kC - 1) / kC);
     return it;
+}
+
+// Steps 4 and 2 for one thread's 32 entries of a chunk row: lambda~ = P + beta (P - Q),
+// lambda = max(0, lambda~ + s rho), rho = (u_h - y_h) + (u_l - y_l) + S; the new lambda
+// overwrites P and its TF32 low part overwrites Q (both 128-byte swizzled).  EDGE adds the
+// zeroing of the diagonal and of padding rows and columns.
+template <bool EDGE>
+__device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, const float (&v)[kC], int r,
+                                          float2 uh2, float2 ul2, float2 beta2, float2 s2, bool rv, int i,
+                                          long long j0, int N) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const int rx = r & 7;
+#pragma unroll
+    for (int g = 0; g < kC / 4; ++g) {  // 16-byte chunk g of the row sits at position g ^ (r % 8)
+        const int off = r * 32 + ((g ^ rx) << 2);
+        const float4 p4 = *reinterpret_cast<const float4 *>(P + off);
+        const float4 q4 = *reinterpret_cast<const float4 *>(Qs + off);
+        const float4 yh = *reinterpret_cast<const float4 *>(Y + 4 * g);
+        const float4 yl = *reinterpret_cast<const float4 *>(Y + kC + 4 * g);
+        const float2 pv[2] = {make_float2(p4.x, p4.y), make_float2(p4.z, p4.w)};
+        const float2 qv[2] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w)};
+        const float2 yhv[2] = {make_float2(yh.x, yh.y), make_float2(yh.z, yh.w)};
+        const float2 ylv[2] = {make_float2(yl.x, yl.y), make_float2(yl.z, yl.w)};
+        float l[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float2 sv = make_float2(v[4 * g + 2 * e], v[4 * g + 2 * e + 1]);
+            const float2 rho = __fadd2_rn(__fadd2_rn(__ffma2_rn(yhv[e], m1, uh2), __ffma2_rn(ylv[e], m1, ul2)), sv);
+            const float2 lt = __ffma2_rn(beta2, __ffma2_rn(qv[e], m1, pv[e]), pv[e]);
+            const float2 w = __ffma2_rn(s2, rho, lt);
+            l[2 * e] = fmaxf(0.f, w.x);
+            l[2 * e + 1] = fmaxf(0.f, w.y);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (EDGE) {
+                const long long j = j0 + 4 * g + e;
+                if (!rv || j >= N || j == i) l[e] = 0.f;
+            }
+            lo[e] = tf32_lo(l[e]);
+        }
+        *reinterpret_cast<float4 *>(P + off) = make_float4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -197,11 +257,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + lambda^k tile stored (2 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
     uint64_t *sfull = lamr + kStages;       // [2] GEMM1 result in S[b]
-    uint64_t *sempty = sfull + 2;           // [2] S[b] read by the epilogue (4 arrivals)
+    uint64_t *sempty = sfull + 2;           // [2] S[b] read by the epilogue group of parity b (4 arrivals)
     uint64_t *xfull = sempty + 2;           // [2] xi rows of an item landed
-    uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item done + u read (5 arrivals)
+    uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item done + u read by every epilogue warp
     uint64_t *afull = xempty + 2;           // [2] accumulator of an item complete
-    uint64_t *aempty = afull + 2;           // [2] accumulator read (4 arrivals)
+    uint64_t *aempty = afull + 2;           // [2] accumulator read (one per warp)
     uint64_t *fin = aempty + 2;             // all MMAs done (teardown)
     int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
     volatile int *abort_flag = ticket + kStages;
@@ -221,9 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             bar_init(&sfull[b], 1);
             bar_init(&sempty[b], 4);
             bar_init(&xfull[b], 1);
-            bar_init(&xempty[b], 5);
+            bar_init(&xempty[b], 1 + kEpiWarps);
             bar_init(&afull[b], 1);
-            bar_init(&aempty[b], 4);
+            bar_init(&aempty[b], kEpiWarps);
         }
         bar_init(fin, 1);
         *abort_flag = 0;
@@ -239,7 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tS[2] = {tmem, tmem + 32}, tA[2] = {tmem + 64, tmem + 96};
+    // tensor-memory columns: S[0], S[1] at 0 and 32, ACC[0], ACC[1] at 64 and 96
+    auto tS = [tmem](int b) { return tmem + 32u * (uint32_t)b; };
+    auto tA = [tmem](int b) { return tmem + 64u + 32u * (uint32_t)b; };
 
     if (warp == 0) {
         // ---------------------------------------------------------------- producer
@@ -307,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
                 const uint32_t ib = su32(item0 + (size_t)xb * kItemBytes);
-                gemm3(tS[b], ib, ib + kTiles, st + kOffXRh, st + kOffXRl, false);
+                gemm3(tS(b), ib, ib + kTiles, st + kOffXRh, st + kOffXRl, false);
                 mma_commit(&sfull[b]);
                 if (g1_c == it.nch - 1) mma_commit(&xempty[xb]);
                 ++g1_c;
@@ -332,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
-                    gemm3(tA[ab], st + kOffP, st + kOffQ, st + kOffXTh, st + kOffXTl, c > 0);
+                    gemm3(tA(ab), st + kOffP, st + kOffQ, st + kOffXTh, st + kOffXTl, c > 0);
                     mma_commit(&empty[s]);
                     if (c == it.nch - 1) mma_commit(&afull[ab]);
                 }
@@ -345,8 +407,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int h = (warp - 2) >> 2;          // group: takes the chunks of parity h
         const int r = 32 * q + lane;            // row within the item
-        const float beta = (float)a.st->beta, sstep = (float)a.st->s;
+        const float2 beta2 = make_float2((float)a.st->beta, (float)a.st->beta);
+        const float2 s2 = make_float2((float)a.st->s, (float)a.st->s);
         uint32_t fill = 0, itn = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
             const Item it = item_of(a, item);
@@ -363,71 +427,62 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncwarp();
             if (lane == 0) bar_arrive(&xempty[xb]);  // the item buffer may be refilled once GEMM1 is done too
+            const float2 uh2 = make_float2(uh, uh), ul2 = make_float2(ul, ul);
             for (int c = 0; c < it.nch; ++c, ++fill) {
                 const int s = fill % kStages, b = fill & 1;
+                if (b != h) continue;  // the other group's chunk
                 const long long j0 = it.c0 + (long long)c * kC;
                 unsigned char *st = stage0 + (size_t)s * kStageBytes;
                 ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, a.err);
                 ok = ok && bar_wait(&sfull[b], fill >> 1, abort_flag, a.err);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-                float lam[32];
+                float v[kC];
                 tc_fence_after();
-                if (ok) tmem_ld32(tS[b] + ((uint32_t)(32 * q) << 16), lam);  // S row r
+                if (ok) tmem_ld32(tS(b) + ((uint32_t)(32 * q) << 16), v);  // S, row r
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) bar_arrive(&sempty[b]);
+                float *P = reinterpret_cast<float *>(st + kOffP);
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(st + kOffY);
-                    float *P = reinterpret_cast<float *>(st + kOffP);
                     float *Qs = reinterpret_cast<float *>(st + kOffQ);
-                    const int rx = r & 7;
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > a.N) ||
                                       (it.i0 + kM > a.N);
-#pragma unroll
-                    for (int g = 0; g < 8; ++g) {  // 16-byte chunk g of the row, swizzled position g ^ (r % 8)
-                        const int off = r * 32 + ((g ^ rx) << 2);
-                        const float4 p4 = *reinterpret_cast<const float4 *>(P + off);
-                        const float4 q4 = *reinterpret_cast<const float4 *>(Qs + off);
-                        const float4 yh = *reinterpret_cast<const float4 *>(Y + 4 * g);
-                        const float4 yl = *reinterpret_cast<const float4 *>(Y + kC + 4 * g);
-                        const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, qv[4] = {q4.x, q4.y, q4.z, q4.w};
-                        const float yhv[4] = {yh.x, yh.y, yh.z, yh.w}, ylv[4] = {yl.x, yl.y, yl.z, yl.w};
-                        float l4[4], lo4[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float rho = ((uh - yhv[e]) + (ul - ylv[e])) + lam[4 * g + e];
-                            const float lt = fmaf(beta, pv[e] - qv[e], pv[e]);
-                            float l = fmaxf(0.f, fmaf(sstep, rho, lt));
-                            if (edge) {
-                                const long long j = j0 + 4 * g + e;
-                                if (!rv || j >= a.N || j == i) l = 0.f;
-                            }
-                            l4[e] = l;
-                            lo4[e] = tf32_lo(l);
-                            lam[4 * g + e] = l;
-                        }
-                        *reinterpret_cast<float4 *>(P + off) = make_float4(l4[0], l4[1], l4[2], l4[3]);
-                        *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo4[0], lo4[1], lo4[2], lo4[3]);
-                    }
+                    if (edge)
+                        epi_chunk<true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N);
+                    else
+                        epi_chunk<false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N);
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
-                    // column sums over this warp's 32 rows: transpose-reduce, lane c ends with column c
-#pragma unroll
-                    for (int w = 16; w >= 1; w >>= 1) {
-                        const bool upper = (lane & w) != 0;
-#pragma unroll
-                        for (int e = 0; e < w; ++e) {
-                            const float send = upper ? lam[e] : lam[e + w];
-                            const float keep = upper ? lam[e + w] : lam[e];
-                            lam[e] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-                        }
-                    }
-                    // after the halving steps lam[0] of lane c is column c summed over the 32 rows
-                    float *colx = reinterpret_cast<float *>(st + kOffColx);
-                    colx[q * kC + lane] = lam[0];
                 }
                 __syncwarp();
                 if (lane == 0) bar_arrive(&lamr[s]);
-                // last warp through: column partials (warp order) and the TMA store of lambda^k
+                if (ok) {
+                    // column sums of this warp's 32 x 32 block, read back from the new tile:
+                    // lane = (row group rg of 8 rows, column group g of 4 columns), then a
+                    // butterfly over the 4 row groups (every lane ends with the same sums)
+                    const int g = lane & 7, rg = lane >> 3;
+                    float2 ca = make_float2(0.f, 0.f), cb = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int rr = 32 * q + 8 * rg + t;
+                        const float4 x = *reinterpret_cast<const float4 *>(P + rr * 32 + ((g ^ (rr & 7)) << 2));
+                        ca = __fadd2_rn(ca, make_float2(x.x, x.y));
+                        cb = __fadd2_rn(cb, make_float2(x.z, x.w));
+                    }
+#pragma unroll
+                    for (int o = 8; o <= 16; o <<= 1) {
+                        const float2 oa = make_float2(__shfl_xor_sync(0xffffffffu, ca.x, o),
+                                                      __shfl_xor_sync(0xffffffffu, ca.y, o));
+                        const float2 ob = make_float2(__shfl_xor_sync(0xffffffffu, cb.x, o),
+                                                      __shfl_xor_sync(0xffffffffu, cb.y, o));
+                        ca = __fadd2_rn(ca, oa);
+                        cb = __fadd2_rn(cb, ob);
+                    }
+                    float *colx = reinterpret_cast<float *>(st + kOffColx);
+                    if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
+                }
+                __syncwarp();
+                // last warp through: column partials (quarter order) and the TMA store of lambda^k
                 int last = 0;
                 if (lane == 0) {
                     __threadfence_block();
@@ -439,15 +494,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __threadfence_block();
                     if (ok && !*abort_flag) {
                         const float *colx = reinterpret_cast<const float *>(st + kOffColx);
-                        const float v = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
+                        const float cv = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
                         const long long j = j0 + lane;
-                        if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = v;
+                        if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = cv;
                     }
                     __syncwarp();
                     if (lane == 0) {
                         ticket[s] = 0;
                         if (ok && !*abort_flag) {
-                            tma_store(&tmQ, st + kOffP, (int)j0, it.i0);
+                            tma_store(&tmQ, P, (int)j0, it.i0);
                             tma_store_wait_read();
                         }
                         bar_arrive(&empty[s]);
@@ -455,20 +510,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // end of item: row partials from the GEMM2 accumulator (columns k < n: sum_j lambda_ij x_jk,
-            // column n: sum_j lambda_ij)
+            // column n: sum_j lambda_ij); this warp holds columns [16 h, 16 h + 16)
             const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, a.err));
-            float acc[32];
+            float acc[kHalf];
             tc_fence_after();
-            if (ok2) tmem_ld32(tA[ab] + ((uint32_t)(32 * q) << 16), acc);
+            if (ok2) tmem_ld16(tA(ab) + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalf * h), acc);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&aempty[ab]);
             if (ok2 && rv) {
                 float *dst = a.rowpart + ((long long)it.sp * a.N + i) * (a.NP + 1);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    if (k < a.n) dst[k] = acc[k];
-                    if (k == a.n) dst[a.NP] = acc[k];
+                for (int e = 0; e < kHalf; ++e) {
+                    const int k = kHalf * h + e;
+                    if (k < a.n) dst[k] = acc[e];
+                    if (k == a.n) dst[a.NP] = acc[e];
                 }
             }
         }
