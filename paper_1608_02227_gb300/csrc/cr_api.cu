@@ -93,6 +93,9 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.col_splits = c->S;
         a.cols_per_split = c->cps;
         a.st = c->st;
+        a.ldv = c->ldv;
+        a.xi_rm = c->xi_rm;
+        a.u = c->uh;
         a.rowpart = (float *)c->rowpart;
         a.colpart = (float *)c->colpart;
         a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
@@ -347,14 +350,10 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(launch_tc_points(c->X, N, n, c->ldv, c->xr, c->xt, c->stream));
         for (int i = 0; i < 2; ++i)
             CR_CUDA(make_tmap_2d(&c->tc_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 32, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 32, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XTh, c->xt, c->ldv, 32, c->ldv, 32, 32, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XTl, c->xt + rm, c->ldv, 32, c->ldv, 32, 32, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 64, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 64, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.Y, c->yh, c->ldv, 2, c->ldv, 32, 2));
-        CR_CUDA(make_tmap_2d(&c->tcm.XIh, c->xi_rm, 32, c->ldv, 32, 32, 128, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XIl, c->xi_rm + rm, 32, c->ldv, 32, 32, 128, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.U, c->uh, c->ldv, 2, c->ldv, 128, 2));
     }
     if (c->tma) {
         for (int i = 0; i < 2; ++i)

@@ -127,21 +127,21 @@ cudaError_t make_tmap_2d(CUtensorMap *tm, const float *base, long long cols, lon
 
 // Tensor-core sweep (cr_sweep_tc.cu, CR_MIXED_TF32): 128-row items, 32-column chunks
 struct TcSweepArgs {
-    long long ld;
+    long long ld, ldv;
     int N, n, NP;
     int row_blocks, col_splits, cols_per_split;
     const DevState *st;
+    const float *xi_rm;      // xi rows [2][ldv][32] (hi, TF32 low part)
+    const float *u;          // u [2][ldv] (hi, lo)
     float *rowpart;          // S x N x (NP+1)
     float *colpart;          // RB x ld (128-row blocks)
     int *err;
 };
 struct TcMaps {
     const CUtensorMap *P, *Q;            // lambda buffers [N][ld], box 32 x 128, 128-byte swizzle
-    CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 32, swizzle
-    CUtensorMap XTh, XTl;                // points transposed + ones row [32][ldv], box 32 x 32, swizzle
+    CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 64, swizzle
+    CUtensorMap XT;                      // points transposed, hi rows (with the ones row) then lo rows [64][ldv], box 32 x 64, swizzle
     CUtensorMap Y;                       // y hi / lo [2][ldv], box 32 x 2
-    CUtensorMap XIh, XIl;                // xi row-major [ldv][32] hi / lo, box 32 x 128, swizzle
-    CUtensorMap U;                       // u hi / lo [2][ldv], box 128 x 2
 };
 cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cudaStream_t s);
 cudaError_t sweep_tc_occupancy(int *blocks_per_sm);

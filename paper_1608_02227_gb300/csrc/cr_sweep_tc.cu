@@ -1,27 +1,35 @@
 // cr_sweep_tc.cu -- the Lambda sweep with both contractions on the tensor cores
 // (CR_MIXED_TF32): Steps 2 and 4 of Figure "papg" (K = N) and the C^T reductions, with
-//     S   = Xi_blk . X_chunk^T      (rho_ij = u_i - y_j + S_ij)          [GEMM1]
-//     ACC += Lambda_blk . [X | 1]_chunk  (row sums of Lambda.X and of Lambda) [GEMM2]
+//     S   = Xi_blk . X_pair^T          (rho_ij = u_i - y_j + S_ij)             [GEMM1]
+//     ACC += Lambda_blk . [X | 1]_chunk    (row sums of Lambda.X and of Lambda)   [GEMM2]
 // as tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory.  TF32 keeps the top
 // 19 bits of each FP32 operand (the hardware truncates), so every operand v is split into
-// hi = v (read as trunc(v)) and lo = v - trunc(v), and each product is formed as
-// hi.hi + hi.lo + lo.hi: close to FP32 accuracy.
+// hi = v (read as trunc(v)) and lo = v - trunc(v):
+//   GEMM1 forms hi.hi + hi.lo + lo.hi with xi (the A operand) held in tensor memory;
+//   GEMM2 stacks the hi and lo parts of [X | 1] along N (N = 64) and runs the hi and the
+//   lo part of Lambda against it, so the accumulator holds Lambda.[X|1]_hi in columns
+//   0..31 and Lambda.X_lo in columns 32..63 (two products instead of three).
+// A tcgen05.mma with M = 128 costs the same for N = 32 and N = 64, so GEMM1 covers two
+// 32-column chunks at once and GEMM2 the two halves of the operand split.
 //
-// CTA = 10 warps, one CTA per SM, work items of 128 rows x one column split, walked in
-// chunks of 32 columns:
+// CTA = 11 warps, one CTA per SM, work items of 128 rows x one column split, walked in
+// chunks of 32 columns (pairs of chunks for GEMM1):
 //   warp 0  producer: 2-D TMA loads (128-byte swizzle) of the lambda^{k-1}, lambda^{k-2}
-//           tiles (128 x 32), the chunk's x rows (hi, lo; 32 x 32), its transposed x with a
-//           row of ones (hi, lo; 32 x 32) and y (hi, lo); per item the xi rows (hi, lo;
-//           128 x 32) and u (hi, lo) -- into a ring of stages guarded by mbarriers;
-//   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 of chunk c+1
-//           is issued before GEMM2 of chunk c, so the epilogue of c overlaps the MMAs;
-//   warps 2-9  epilogue in two groups of four that take alternate chunks (two chunks in
-//           flight), thread = row (tensor-memory lane): reads S from tensor memory, forms
-//           lambda^k (packed FP32x2 arithmetic), writes it over the consumed lambda^{k-1}
-//           tile (it is the A operand of GEMM2 and the source of the TMA store of lambda^k)
-//           and its low part over the lambda^{k-2} tile, sums its 32 x 32 block of the new
-//           tile by columns, and at the end of an item reads half of the GEMM2 accumulator
-//           (row partials).
+//           tiles (128 x 32), the chunk's transposed points with a row of ones (hi rows
+//           then lo rows; 64 x 32) and y (hi, lo), into a ring of stages;
+//   warp 10 second producer: the point rows of each chunk pair (hi, lo; 64 x 32 each)
+//           for GEMM1, in their own ring, freed as soon as GEMM1 is done;
+//   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 runs up to
+//           three pairs ahead of GEMM2 (four S tiles in tensor memory), issued as soon as
+//           its inputs land, so the epilogue does not wait for it;
+//   warps 2-9  epilogue in two groups of four (one warp per tensor-memory lane quarter)
+//           that take the even and the odd chunks of an item, thread = row: reads S from
+//           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
+//           consumed lambda^{k-1} tile (A operand of GEMM2, source of the TMA store of
+//           lambda^k) and its TF32 low part over the lambda^{k-2} tile, sums its 32 x 32
+//           block of the new tile by columns; the first group also copies the xi rows of
+//           the next item into tensor memory; at the end of an item both groups read the
+//           GEMM2 accumulator (row partials).
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -32,25 +40,34 @@ namespace cr {
 namespace {
 
 constexpr int kM = 128;       // rows per item (MMA M, tensor-memory lanes)
-constexpr int kC = 32;        // columns per chunk (GEMM1 N, GEMM2 K)
-constexpr int kK = 32;        // GEMM1 K (point dimension padded) and GEMM2 N
-constexpr int kStages = 3;
+constexpr int kC = 32;        // columns per chunk (GEMM2 K)
+constexpr int kK = 32;        // point dimension padded (GEMM1 K)
+constexpr int kStages = 4;    // ring of lambda / transposed-point stages
+constexpr int kXr = 2;        // ring of point-row pair tiles (GEMM1 B operand)
+constexpr int kSBufs = 4;     // pair S tiles in tensor memory
 constexpr int kTiles = kM * kC * 4;             // bytes of one 128 x 32 FP32 tile (16 KB)
-constexpr int kSmall = kC * kK * 4;             // bytes of one 32 x 32 FP32 tile (4 KB)
-// stage layout (bytes): P | Q | XRh | XRl | XTh | XTl | Y(hi 32, lo 32) | colx[4][32] | pad
-constexpr int kOffP = 0, kOffQ = kTiles, kOffXRh = 2 * kTiles, kOffXRl = kOffXRh + kSmall;
-constexpr int kOffXTh = kOffXRl + kSmall, kOffXTl = kOffXTh + kSmall, kOffY = kOffXTl + kSmall;
-constexpr int kOffColx = kOffY + 2 * kC * 4;
-constexpr int kStageBytes = ((kOffColx + 4 * kC * 4 + 1023) / 1024) * 1024;
-constexpr int kTxStage = 2 * kTiles + 4 * kSmall + 2 * kC * 4;
-// item buffer: XIh | XIl | U(hi 128, lo 128)
-constexpr int kItemBytes = ((2 * kTiles + 2 * kM * 4 + 1023) / 1024) * 1024;
-constexpr int kTxItem = 2 * kTiles + 2 * kM * 4;
-constexpr int kEpiWarps = 8;                  // two groups of four (one warp per lane quarter)
+constexpr int kXtBytes = 2 * kK * kC * 4;       // transposed points, hi and lo rows (64 x 32, 8 KB)
+// stage layout (bytes): P | Q | XT; y (hi 32, lo 32) and the column partials of each
+// stage sit in small arrays after the point-row ring
+constexpr int kOffP = 0, kOffQ = kTiles, kOffXT = 2 * kTiles;
+constexpr int kStageBytes = 2 * kTiles + kXtBytes;
+constexpr int kYBytes = 2 * kC * 4, kColxBytes = 4 * kC * 4;
+constexpr int kTxStage = kStageBytes + kYBytes;
+constexpr int kXrHalf = 2 * kC * kK * 4;        // one 64 x 32 point-row tile (8 KB)
+constexpr int kXrBytes = 2 * kXrHalf;           // hi | lo
+constexpr int kEpiWarps = 8;                    // two groups of four (one warp per lane quarter)
 constexpr int kHalf = kC / 2;                   // accumulator columns read by each group
-constexpr int kThreads = (2 + kEpiWarps) * 32;
-constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kItemBytes + 512;
-constexpr uint32_t kTmemCols = 128;             // S[2] (2 x 32) + ACC[2] (2 x 32)
+constexpr int kXrWarp = 2 + kEpiWarps;          // second producer
+constexpr int kThreads = (3 + kEpiWarps) * 32;
+constexpr size_t kSmemData =
+    (size_t)kStages * kStageBytes + (size_t)kXr * kXrBytes + (size_t)kStages * (kYBytes + kColxBytes);
+constexpr size_t kSmem = 1024 + kSmemData + 512;
+static_assert(kStageBytes % 1024 == 0 && kXrBytes % 1024 == 0, "swizzled tiles keep 1024-byte alignment");
+static_assert(kSmem <= 232448, "shared memory budget");
+// tensor memory: S[b] (64 columns each) at 64 b, ACC[0..1] (64 each) at 256, XI[0..1]
+// (hi 32 + lo 32 each) at 384
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 128u;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
 
@@ -66,6 +83,9 @@ __device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count) {
 __device__ __forceinline__ void bar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+__device__ __forceinline__ void bar_arrive_n(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
 __device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
@@ -75,6 +95,16 @@ __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t ph) {
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(su32(b)), "r"(ph), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+// non-blocking test of the same condition
+__device__ __forceinline__ bool bar_test(uint64_t *b, uint32_t ph) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(ph)
         : "memory");
     return ok != 0;
 }
@@ -129,29 +159,45 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;              // 128-byte swizzle
     return d;
 }
-// kind::tf32, D = F32, A and B TF32 K-major, M = 128, N = 32
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+// kind::tf32, D = F32, A and B TF32 K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, bool acc) {
+__device__ __forceinline__ void mma_ss(uint32_t tmem_d, uint64_t ad, uint64_t bd, bool acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(ad), "l"(bd), "r"(kIdesc), "r"((uint32_t)acc)
         : "memory");
 }
+__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bd), "r"(kIdesc), "r"((uint32_t)acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                  : "memory");
 }
-// D (+)= sum over (A_hi, B_hi), (A_hi, B_lo), (A_lo, B_hi) of A . B^T, K = 32 in 4 steps
-__device__ __forceinline__ void gemm3(uint32_t tmem_d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
-                                      bool acc_first) {
-    const uint32_t A[3] = {ah, ah, al}, B[3] = {bh, bl, bh};
+// GEMM1: S = xi_hi.x_hi + xi_hi.x_lo + xi_lo.x_hi, xi in tensor memory (hi at column a,
+// lo at a + 32), the pair's point rows in shared memory (hi tile at bh, lo at bl)
+__device__ __forceinline__ void gemm1(uint32_t tmem_d, uint32_t a, uint32_t bh, uint32_t bl) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p) {
+        const uint32_t A = p < 2 ? a : a + 32u, B = p == 1 ? bl : bh;
 #pragma unroll
-        for (int k = 0; k < kK / 8; ++k)
-            mma(tmem_d, sdesc(A[p] + 32 * k), sdesc(B[p] + 32 * k), acc_first || p > 0 || k > 0);
+        for (int k = 0; k < kK / 8; ++k) mma_ts(tmem_d, A + 8u * k, sdesc(B + 32 * k), p > 0 || k > 0);
+    }
+}
+// GEMM2: ACC (+)= lambda_hi.[X|1 ; X_lo] + lambda_lo.[X|1 ; X_lo] over the chunk's 32 columns
+__device__ __forceinline__ void gemm2(uint32_t tmem_d, uint32_t ah, uint32_t al, uint32_t b, bool acc_first) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const uint32_t A = p == 0 ? ah : al;
+#pragma unroll
+        for (int k = 0; k < kC / 8; ++k) mma_ss(tmem_d, sdesc(A + 32 * k), sdesc(b + 32 * k), acc_first || p > 0 || k > 0);
+    }
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
@@ -177,6 +223,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
+        "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+        "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
+        "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
 }
 __device__ __forceinline__ float tf32_lo(float v) { return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
@@ -243,24 +303,26 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
 __global__ void __launch_bounds__(kThreads, 1)
     sweep_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
                     const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
-                    const __grid_constant__ CUtensorMap tmXTh, const __grid_constant__ CUtensorMap tmXTl,
-                    const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmXIh,
-                    const __grid_constant__ CUtensorMap tmXIl, const __grid_constant__ CUtensorMap tmU,
+                    const __grid_constant__ CUtensorMap tmXT, const __grid_constant__ CUtensorMap tmY,
                     const TcSweepArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *stage0 = base;
-    unsigned char *item0 = base + (size_t)kStages * kStageBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(item0 + 2 * (size_t)kItemBytes);
+    unsigned char *xr0 = base + (size_t)kStages * kStageBytes;
+    unsigned char *y0 = xr0 + (size_t)kXr * kXrBytes;
+    unsigned char *colx0 = y0 + (size_t)kStages * kYBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(colx0 + (size_t)kStages * kColxBytes);
     uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
     uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + lambda^k tile stored (2 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
-    uint64_t *sfull = lamr + kStages;       // [2] GEMM1 result in S[b]
-    uint64_t *sempty = sfull + 2;           // [2] S[b] read by the epilogue group of parity b (4 arrivals)
-    uint64_t *xfull = sempty + 2;           // [2] xi rows of an item landed
-    uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item done + u read by every epilogue warp
-    uint64_t *afull = xempty + 2;           // [2] accumulator of an item complete
+    uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a pair in S[b]
+    uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by both epilogue groups (8 arrivals)
+    uint64_t *xfull = sempty + kSBufs;      // [2] xi rows of an item in tensor memory (4 arrivals)
+    uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item that used them done
+    uint64_t *rfull = xempty + 2;           // [kXr] point-row pair tiles landed
+    uint64_t *rempty = rfull + kXr;         // [kXr] GEMM1 that read them done
+    uint64_t *afull = rempty + kXr;         // [2] accumulator of an item complete
     uint64_t *aempty = afull + 2;           // [2] accumulator read (one per warp)
     uint64_t *fin = aempty + 2;             // all MMAs done (teardown)
     int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
@@ -277,13 +339,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             bar_init(&lamr[s], 4);
             ticket[s] = 0;
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kSBufs; ++b) {
             bar_init(&sfull[b], 1);
-            bar_init(&sempty[b], 4);
-            bar_init(&xfull[b], 1);
-            bar_init(&xempty[b], 1 + kEpiWarps);
+            bar_init(&sempty[b], kEpiWarps);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&xfull[b], 4);
+            bar_init(&xempty[b], 1);
             bar_init(&afull[b], 1);
             bar_init(&aempty[b], kEpiWarps);
+        }
+        for (int b = 0; b < kXr; ++b) {
+            bar_init(&rfull[b], 1);
+            bar_init(&rempty[b], 1);
         }
         bar_init(fin, 1);
         *abort_flag = 0;
@@ -299,24 +367,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // tensor-memory columns: S[0], S[1] at 0 and 32, ACC[0], ACC[1] at 64 and 96
-    auto tS = [tmem](int b) { return tmem + 32u * (uint32_t)b; };
-    auto tA = [tmem](int b) { return tmem + 64u + 32u * (uint32_t)b; };
+    auto tS = [tmem](int b) { return tmem + 64u * (uint32_t)b; };
+    auto tA = [tmem](int b) { return tmem + kColAcc + 64u * (uint32_t)b; };
+    auto tX = [tmem](int b) { return tmem + kColXi + 64u * (uint32_t)b; };
 
     if (warp == 0) {
-        // ---------------------------------------------------------------- producer
+        // ---------------------------------------------------------------- stage producer
         if (lane == 0) {
-            uint32_t fill = 0, itn = 0;
+            uint32_t fill = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
                 const Item it = item_of(a, item);
-                const int xb = itn & 1;
-                unsigned char *ib = item0 + (size_t)xb * kItemBytes;
-                if (!slot_wait(&xempty[xb], itn >> 1, abort_flag, a.err)) break;
-                bar_expect(&xfull[xb], kTxItem);
-                tma_load(ib, &tmXIh, &xfull[xb], 0, it.i0);
-                tma_load(ib + kTiles, &tmXIl, &xfull[xb], 0, it.i0);
-                tma_load(ib + 2 * kTiles, &tmU, &xfull[xb], it.i0, 0);
                 for (int c = 0; c < it.nch; ++c, ++fill) {
                     const int s = fill % kStages;
                     const int j0 = (int)(it.c0 + (long long)c * kC);
@@ -328,11 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     bar_expect(&full[s], kTxStage);
                     tma_load(st + kOffP, &tmP, &full[s], j0, it.i0);
                     tma_load(st + kOffQ, &tmQ, &full[s], j0, it.i0);
-                    tma_load(st + kOffXRh, &tmXRh, &full[s], 0, j0);
-                    tma_load(st + kOffXRl, &tmXRl, &full[s], 0, j0);
-                    tma_load(st + kOffXTh, &tmXTh, &full[s], j0, 0);
-                    tma_load(st + kOffXTl, &tmXTl, &full[s], j0, 0);
-                    tma_load(st + kOffY, &tmY, &full[s], j0, 0);
+                    tma_load(st + kOffXT, &tmXT, &full[s], j0, 0);
+                    tma_load(y0 + (size_t)s * kYBytes, &tmY, &full[s], j0, 0);
                 }
             }
             // drain the copies still in flight before the CTA can exit
@@ -342,49 +400,86 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+    } else if (warp == kXrWarp) {
+        // ---------------------------------------------------------------- point-row producer
+        if (lane == 0) {
+            uint32_t pf = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+                const Item it = item_of(a, item);
+                for (int pc = 0; 2 * pc < it.nch; ++pc, ++pf) {
+                    const int x = pf % kXr;
+                    const int j0 = (int)(it.c0 + (long long)pc * 2 * kC);
+                    if (!slot_wait(&rempty[x], pf / kXr, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *xr = xr0 + (size_t)x * kXrBytes;
+                    bar_expect(&rfull[x], kXrBytes);
+                    tma_load(xr, &tmXRh, &rfull[x], 0, j0);
+                    tma_load(xr + kXrHalf, &tmXRl, &rfull[x], 0, j0);
+                }
+            }
+            for (uint32_t f = pf > (uint32_t)kXr ? pf - kXr : 0; f < pf; ++f) {
+                const uint64_t t0 = gtimer();
+                while (!bar_try(&rfull[f % kXr], (f / kXr) & 1u) && gtimer() - t0 < 200000000ull) {
+                }
+            }
+        }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            // flattened (item, chunk) sequence of this CTA; GEMM1(f+1) is issued before GEMM2(f)
-            uint32_t fill = 0, itn = 0;
+            uint32_t fill = 0, itn = 0, cur_pair = 0;
             bool ok = true;
-            // GEMM1 state: next fill to issue
-            int g1_item = blockIdx.x, g1_c = 0;
-            uint32_t g1_fill = 0, g1_itn = 0;
-            auto issue_gemm1 = [&](void) -> bool {
-                // advance to a valid (item, chunk)
+            // GEMM1 state: the next pair to issue (flattened index g1_pair)
+            int g1_item = blockIdx.x, g1_pc = 0;
+            uint32_t g1_pair = 0, g1_itn = 0;
+            auto g1_norm = [&](void) -> bool {  // advance to a valid (item, pair); false at the end
                 while (g1_item < items) {
-                    const Item it = item_of(a, g1_item);
-                    if (g1_c < it.nch) break;
+                    if (2 * g1_pc < item_of(a, g1_item).nch) return true;
                     g1_item += gridDim.x;
-                    g1_c = 0;
+                    g1_pc = 0;
                     ++g1_itn;
                 }
-                if (g1_item >= items) return true;
+                return false;
+            };
+            auto g1_ready = [&](void) -> bool {  // inputs of the next GEMM1 present (no waiting)
+                const int x = g1_pair % kXr, b = g1_pair % kSBufs;
+                if (!bar_test(&rfull[x], (g1_pair / kXr) & 1u)) return false;
+                if (g1_pc == 0 && !bar_test(&xfull[g1_itn & 1], (g1_itn >> 1) & 1u)) return false;
+                return g1_pair < (uint32_t)kSBufs || bar_test(&sempty[b], (g1_pair / kSBufs - 1) & 1u);
+            };
+            auto issue_gemm1 = [&](void) -> bool {
                 const Item it = item_of(a, g1_item);
-                const int s = g1_fill % kStages, b = g1_fill & 1, xb = g1_itn & 1;
-                if (!bar_wait(&full[s], g1_fill / kStages, abort_flag, a.err)) return false;
-                if (g1_c == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, a.err)) return false;
-                if (!slot_wait(&sempty[b], g1_fill >> 1, abort_flag, a.err)) return false;
+                const int x = g1_pair % kXr, b = g1_pair % kSBufs, xb = g1_itn & 1;
+                if (!bar_wait(&rfull[x], g1_pair / kXr, abort_flag, a.err)) return false;
+                if (g1_pc == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, a.err)) return false;
+                if (!slot_wait(&sempty[b], g1_pair / kSBufs, abort_flag, a.err)) return false;
                 tc_fence_after();
-                const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
-                const uint32_t ib = su32(item0 + (size_t)xb * kItemBytes);
-                gemm3(tS(b), ib, ib + kTiles, st + kOffXRh, st + kOffXRl, false);
+                const uint32_t xr = su32(xr0 + (size_t)x * kXrBytes);
+                gemm1(tS(b), tX(xb), xr, xr + kXrHalf);
                 mma_commit(&sfull[b]);
-                if (g1_c == it.nch - 1) mma_commit(&xempty[xb]);
-                ++g1_c;
-                ++g1_fill;
+                mma_commit(&rempty[x]);
+                if (2 * (g1_pc + 1) >= it.nch) mma_commit(&xempty[xb]);
+                ++g1_pc;
+                ++g1_pair;
                 return true;
             };
-            ok = issue_gemm1();
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
                 const Item it = item_of(a, item);
                 const int ab = itn & 1;
                 for (int c = 0; c < it.nch && ok; ++c, ++fill) {
-                    ok = issue_gemm1();  // GEMM1 of the next chunk (if any)
+                    if (c > 0 && (c & 1) == 0) ++cur_pair;
+                    // GEMM1 runs ahead by up to kSBufs - 1 pairs: it waits only for the pair
+                    // whose epilogue comes next, and later ones go in as their inputs land
+                    while (ok && g1_pair < cur_pair + (uint32_t)kSBufs && g1_norm()) {
+                        if (g1_pair > cur_pair && !g1_ready()) break;
+                        ok = issue_gemm1();
+                    }
                     if (!ok) break;
                     const int s = fill % kStages;
-                    if (!bar_wait(&lamr[s], fill / kStages, abort_flag, a.err)) {
+                    if (!bar_wait(&full[s], fill / kStages, abort_flag, a.err) ||
+                        !bar_wait(&lamr[s], fill / kStages, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
@@ -394,10 +489,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
-                    gemm3(tA(ab), st + kOffP, st + kOffQ, st + kOffXTh, st + kOffXTl, c > 0);
+                    gemm2(tA(ab), st + kOffP, st + kOffQ, st + kOffXT, c > 0);
                     mma_commit(&empty[s]);
                     if (c == it.nch - 1) mma_commit(&afull[ab]);
                 }
+                ++cur_pair;  // the next item starts a new pair
             }
             mma_commit(fin);
             const uint64_t t0 = gtimer();
@@ -407,44 +503,73 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-        const int h = (warp - 2) >> 2;          // group: takes the chunks of parity h
+        const int h = (warp - 2) >> 2;          // group: takes the chunks of parity h in an item
         const int r = 32 * q + lane;            // row within the item
+        const uint32_t lq = (uint32_t)(32 * q) << 16;
         const float2 beta2 = make_float2((float)a.st->beta, (float)a.st->beta);
         const float2 s2 = make_float2((float)a.st->s, (float)a.st->s);
-        uint32_t fill = 0, itn = 0;
+        // the first group copies the xi rows (hi, lo) of an item into tensor-memory buffer
+        // xitn & 1, once the GEMM1s of the item that used that buffer before are done
+        auto put_xi = [&](int item, uint32_t xitn) -> bool {
+            const int xb = xitn & 1;
+            const bool ok = __all_sync(0xffffffffu, slot_wait(&xempty[xb], xitn >> 1, abort_flag, a.err));
+            if (ok) {
+                const long long row = (long long)item_of(a, item).i0 + r;  // < ldv
+                const float4 *hi = reinterpret_cast<const float4 *>(a.xi_rm + row * 32);
+                const float4 *lo = reinterpret_cast<const float4 *>(a.xi_rm + a.ldv * 32 + row * 32);
+                float v[32];
+                tc_fence_after();
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float4 w = __ldg(hi + t);
+                    v[4 * t] = w.x, v[4 * t + 1] = w.y, v[4 * t + 2] = w.z, v[4 * t + 3] = w.w;
+                }
+                tmem_st32(tX(xb) + lq, v);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float4 w = __ldg(lo + t);
+                    v[4 * t] = w.x, v[4 * t + 1] = w.y, v[4 * t + 2] = w.z, v[4 * t + 3] = w.w;
+                }
+                tmem_st32(tX(xb) + 32u + lq, v);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&xfull[xb]);
+            return ok;
+        };
+        uint32_t fill = 0, itn = 0, pair = 0;
+        bool ok = true;
+        if (h == 0 && blockIdx.x < items) ok = put_xi(blockIdx.x, 0);
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
             const Item it = item_of(a, item);
-            const int xb = itn & 1, ab = itn & 1;
+            const int ab = itn & 1;
             const int i = it.i0 + r;
             const bool rv = i < a.N;
-            const unsigned char *ib = item0 + (size_t)xb * kItemBytes;
-            float uh = 0.f, ul = 0.f;
-            bool ok = __all_sync(0xffffffffu, bar_wait(&xfull[xb], itn >> 1, abort_flag, a.err));
-            if (ok) {
-                const float *U = reinterpret_cast<const float *>(ib + 2 * kTiles);
-                uh = U[r];
-                ul = U[kM + r];
-            }
-            __syncwarp();
-            if (lane == 0) bar_arrive(&xempty[xb]);  // the item buffer may be refilled once GEMM1 is done too
+            // xi rows of the next item go into the other tensor-memory buffer now, so that
+            // GEMM1 can run ahead across the item boundary
+            if (h == 0 && item + (int)gridDim.x < items) ok = put_xi(item + gridDim.x, itn + 1) && ok;
+            const float uh = a.u[i], ul = a.u[a.ldv + i];  // i < ldv
             const float2 uh2 = make_float2(uh, uh), ul2 = make_float2(ul, ul);
             for (int c = 0; c < it.nch; ++c, ++fill) {
-                const int s = fill % kStages, b = fill & 1;
-                if (b != h) continue;  // the other group's chunk
+                if (c > 0 && (c & 1) == 0) ++pair;
+                if ((c & 1) != h) continue;  // the other group's chunk
+                const int s = fill % kStages, b = pair % kSBufs;
                 const long long j0 = it.c0 + (long long)c * kC;
                 unsigned char *st = stage0 + (size_t)s * kStageBytes;
                 ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, a.err);
-                ok = ok && bar_wait(&sfull[b], fill >> 1, abort_flag, a.err);
+                ok = ok && bar_wait(&sfull[b], pair / kSBufs, abort_flag, a.err);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
                 float v[kC];
                 tc_fence_after();
-                if (ok) tmem_ld32(tS(b) + ((uint32_t)(32 * q) << 16), v);  // S, row r
+                if (ok) tmem_ld32(tS(b) + 32u * (uint32_t)(c & 1) + lq, v);  // S, row r, this chunk's half
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) bar_arrive(&sempty[b]);
+                // a pair with one chunk (odd count at the end of an item) is released for both groups
+                if (lane == 0) bar_arrive_n(&sempty[b], (c + 1 < it.nch || (c & 1)) ? 1u : 2u);
                 float *P = reinterpret_cast<float *>(st + kOffP);
                 if (ok) {
-                    const float *Y = reinterpret_cast<const float *>(st + kOffY);
+                    const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
                     float *Qs = reinterpret_cast<float *>(st + kOffQ);
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > a.N) ||
                                       (it.i0 + kM > a.N);
@@ -478,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ca = __fadd2_rn(ca, oa);
                         cb = __fadd2_rn(cb, ob);
                     }
-                    float *colx = reinterpret_cast<float *>(st + kOffColx);
+                    float *colx = reinterpret_cast<float *>(colx0 + (size_t)s * kColxBytes);
                     if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
                 }
                 __syncwarp();
@@ -493,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (last) {
                     __threadfence_block();
                     if (ok && !*abort_flag) {
-                        const float *colx = reinterpret_cast<const float *>(st + kOffColx);
+                        const float *colx = reinterpret_cast<const float *>(colx0 + (size_t)s * kColxBytes);
                         const float cv = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
                         const long long j = j0 + lane;
                         if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = cv;
@@ -509,12 +634,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             }
-            // end of item: row partials from the GEMM2 accumulator (columns k < n: sum_j lambda_ij x_jk,
-            // column n: sum_j lambda_ij); this warp holds columns [16 h, 16 h + 16)
+            ++pair;  // the next item starts a new pair
+            // end of item: row partials from the GEMM2 accumulator: columns k < n of the two
+            // halves give sum_j lambda_ij x_jk, column n of the first gives sum_j lambda_ij;
+            // this group reads columns [16 h, 16 h + 16) of both halves
             const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, a.err));
-            float acc[kHalf];
+            float acc[kHalf], acl[kHalf];
             tc_fence_after();
-            if (ok2) tmem_ld16(tA(ab) + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalf * h), acc);
+            if (ok2) {
+                tmem_ld16(tA(ab) + lq + (uint32_t)(kHalf * h), acc);
+                tmem_ld16(tA(ab) + lq + 32u + (uint32_t)(kHalf * h), acl);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&aempty[ab]);
@@ -523,10 +653,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int e = 0; e < kHalf; ++e) {
                     const int k = kHalf * h + e;
-                    if (k < a.n) dst[k] = acc[e];
+                    if (k < a.n) dst[k] = acc[e] + acl[e];
                     if (k == a.n) dst[a.NP] = acc[e];
                 }
             }
+            ok = ok && ok2;
         }
         tma_store_wait_all();
     }
@@ -556,7 +687,7 @@ cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cud
     int occ = 0;
     cudaError_t e = sweep_tc_occupancy(&occ);
     if (e != cudaSuccess) return e;
-    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, m.XRh, m.XRl, m.XTh, m.XTl, m.Y, m.XIh, m.XIl, m.U, a);
+    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, m.XRh, m.XRl, m.XT, m.Y, a);
     return cudaGetLastError();
 }
 
