@@ -102,6 +102,7 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         TcMaps m = c->tcm;
         m.P = &c->tc_lam[P];
         m.Q = &c->tc_lam[Q];
+        m.Qs = &c->tc_lam32[Q];
         CR_CUDA(launch_sweep_tc(m, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
@@ -350,6 +351,8 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(launch_tc_points(c->X, N, n, c->ldv, c->xr, c->xt, c->stream));
         for (int i = 0; i < 2; ++i)
             CR_CUDA(make_tmap_2d(&c->tc_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
+        for (int i = 0; i < 2; ++i)
+            CR_CUDA(make_tmap_2d(&c->tc_lam32[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 32, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));

@@ -45,7 +45,7 @@ struct cr_ctx {
     CUtensorMap tm_lam[2];
     TmaMaps tm{};
     bool tc = false;             // CR_MIXED_TF32: tensor-core sweep (cr_sweep_tc.cu)
-    CUtensorMap tc_lam[2];
+    CUtensorMap tc_lam[2], tc_lam32[2];
     TcMaps tcm{};
     float *xr = nullptr, *xt = nullptr, *xi_rm = nullptr;
     // graph of graph_iters iterations starting at an even k

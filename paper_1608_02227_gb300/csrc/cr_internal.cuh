@@ -139,6 +139,7 @@ struct TcSweepArgs {
 };
 struct TcMaps {
     const CUtensorMap *P, *Q;            // lambda buffers [N][ld], box 32 x 128, 128-byte swizzle
+    const CUtensorMap *Qs;               // the lambda^k buffer with a 32 x 32 box (per-warp stores)
     CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 64, swizzle
     CUtensorMap XT;                      // points transposed, hi rows (with the ones row) then lo rows [64][ldv], box 32 x 64, swizzle
     CUtensorMap Y;                       // y hi / lo [2][ldv], box 32 x 2

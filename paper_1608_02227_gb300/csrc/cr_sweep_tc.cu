@@ -25,11 +25,11 @@
 //   warps 2-9  epilogue in two groups of four (one warp per tensor-memory lane quarter)
 //           that take the even and the odd chunks of an item, thread = row: reads S from
 //           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
-//           consumed lambda^{k-1} tile (A operand of GEMM2, source of the TMA store of
-//           lambda^k) and its TF32 low part over the lambda^{k-2} tile, sums its 32 x 32
-//           block of the new tile by columns; the first group also copies the xi rows of
-//           the next item into tensor memory; at the end of an item both groups read the
-//           GEMM2 accumulator (row partials).
+//           consumed lambda^{k-1} tile (A operand of GEMM2 and source of the warp's TMA
+//           store of its 32 rows of lambda^k) and its TF32 low part over the lambda^{k-2}
+//           tile, sums its 32 x 32 block of the new tile by columns; the first group also
+//           copies the xi rows of the next item into tensor memory; at the end of an item
+//           both groups read the GEMM2 accumulator (row partials).
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -302,6 +302,7 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
 
 __global__ void __launch_bounds__(kThreads, 1)
     sweep_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
+                    const __grid_constant__ CUtensorMap tmQs,
                     const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
                     const __grid_constant__ CUtensorMap tmXT, const __grid_constant__ CUtensorMap tmY,
                     const TcSweepArgs a) {
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *colx0 = y0 + (size_t)kStages * kYBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(colx0 + (size_t)kStages * kColxBytes);
     uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
-    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + lambda^k tile stored (2 arrivals)
+    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + each warp's lambda^k rows stored (5 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
     uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a pair in S[b]
     uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by both epilogue groups (8 arrivals)
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             bar_init(&full[s], 1);
-            bar_init(&empty[s], 2);
+            bar_init(&empty[s], 5);
             bar_init(&lamr[s], 4);
             ticket[s] = 0;
         }
@@ -580,7 +581,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
                 }
                 __syncwarp();
-                if (lane == 0) bar_arrive(&lamr[s]);
+                if (lane == 0) {
+                    // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
+                    if (ok && it.i0 + 32 * q < a.N) tma_store(&tmQs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
+                    bar_arrive(&lamr[s]);
+                }
                 if (ok) {
                     // column sums of this warp's 32 x 32 block, read back from the new tile:
                     // lane = (row group rg of 8 rows, column group g of 4 columns), then a
@@ -607,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
                 }
                 __syncwarp();
-                // last warp through: column partials (quarter order) and the TMA store of lambda^k
+                // last warp through: column partials in quarter order
                 int last = 0;
                 if (lane == 0) {
                     __threadfence_block();
@@ -624,14 +629,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = cv;
                     }
                     __syncwarp();
-                    if (lane == 0) {
-                        ticket[s] = 0;
-                        if (ok && !*abort_flag) {
-                            tma_store(&tmQ, P, (int)j0, it.i0);
-                            tma_store_wait_read();
-                        }
-                        bar_arrive(&empty[s]);
-                    }
+                    if (lane == 0) ticket[s] = 0;
+                }
+                if (lane == 0) {
+                    tma_store_wait_read();  // the stage may be refilled once the store has read it
+                    bar_arrive(&empty[s]);
                 }
             }
             ++pair;  // the next item starts a new pair
@@ -687,7 +689,7 @@ cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cud
     int occ = 0;
     cudaError_t e = sweep_tc_occupancy(&occ);
     if (e != cudaSuccess) return e;
-    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, m.XRh, m.XRl, m.XT, m.Y, a);
+    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, *m.Qs, m.XRh, m.XRl, m.XT, m.Y, a);
     return cudaGetLastError();
 }
 
