@@ -40,6 +40,7 @@ METRIC = "lambda_pair_updates_per_s"
 UNIT = "pairs/s"
 GAMMA = 1e-4
 CPU_SAMPLE_N = 8000  # oracle sample: the first 8000 points of the same instance
+REF_BUDGET_S = 90.0  # --impl reference: target seconds of oracle work for warm-up + steps
 
 
 def _peaks():
@@ -70,6 +71,10 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()  # the timed region starts once samples are flowing
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()
         except (FileNotFoundError, OSError):
             self.proc = None
 
@@ -118,7 +123,15 @@ def run_reference(args):
     import oracle
 
     inst = cr_synth.workload(args.workload)
-    Ns = min(CPU_SAMPLE_N, inst.N)
+    # bounded sample: the oracle's cost per iteration grows as N^2, so the sample size is
+    # chosen from a one-iteration calibration to keep warm-up + steps near REF_BUDGET_S
+    n0 = min(1000, inst.N)
+    oc = oracle.PAPG(inst.X[:n0], inst.ybar[:n0], GAMMA, oracle.lipschitz(inst.X[:n0], GAMMA))
+    t0 = time.perf_counter()
+    oc.step(1, log=False)
+    t1 = max(time.perf_counter() - t0, 1e-6)
+    scale = (REF_BUDGET_S / (args.steps + args.warmup) / t1) ** 0.5
+    Ns = int(max(200, min(CPU_SAMPLE_N, inst.N, n0 * scale)) // 100 * 100)
     X, yb = inst.X[:Ns], inst.ybar[:Ns]
     L = oracle.lipschitz(X, GAMMA)
     o = oracle.PAPG(X, yb, GAMMA, L)
@@ -265,12 +278,14 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="lse_N20000_n20")
     ap.add_argument("--N", type=int, default=0, help="shrink the workload to its first N points (profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "fp64", "tf32"],
+                    help="tf32: FP32 multipliers with hi+lo TF32 tensor-core contractions (the mixed-precision "
+                         "configuration of the N = 20000 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "batch", "serve"],
                     help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances; "
