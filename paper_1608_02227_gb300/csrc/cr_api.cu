@@ -399,6 +399,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     h.beta = 0.0;
     h.s = 1.0 / c->L;
     h.gamma = c->opt.gamma;
+    h.inv_gamma = 1.0 / c->opt.gamma;
     h.k = 0;
     h.accelerate = c->opt.accelerate ? 1 : 0;
     CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));

@@ -17,6 +17,32 @@ __device__ __forceinline__ void split_hi_lo(double v, float *hi, float *lo) {
     *lo = (float)(v - (double)h);
 }
 
+// Sum over the column splits of entry e of point l's row partials.  FP32 partials are
+// added in FP32 in groups of 8 (pairwise; error ~3 ulp of the group, the level of the FP32
+// multipliers themselves) and the groups in FP64: GB300's FP64 pipe bounds this kernel
+// otherwise.  FP64 partials are summed in FP64.
+template <typename PT>
+__device__ __forceinline__ double split_sum(const PT *rowp, int S, long long N, long long l, int W, int e) {
+    if constexpr (sizeof(PT) == 8) {
+        double s = 0.0;
+        for (int sp = 0; sp < S; ++sp) s += rowp[((long long)sp * N + l) * W + e];
+        return s;
+    } else {
+        double s = 0.0;
+        int sp = 0;
+        for (; sp + 8 <= S; sp += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = rowp[((long long)(sp + u) * N + l) * W + e];
+            s += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+        }
+        if (sp == S) return s;
+        float t = 0.f;
+        for (; sp < S; ++sp) t += rowp[((long long)sp * N + l) * W + e];
+        return s + (double)t;
+    }
+}
+
 constexpr int kFX = 32;   // points per CTA
 constexpr int kFY = 8;    // slices per point (row blocks, components)
 
@@ -29,10 +55,16 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
     const int l = blk * kFX + tx;
     const bool valid = l < a.N;
     DevState *st = a.st;
-    const double gamma = st->gamma;
-    const double tk = st->t;
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));               // Step 3
-    const double beta = (st->accelerate && !a.init) ? (tk - 1.0) / tn : 0.0;  // Step 4 coefficient
+    const double gamma = st->gamma, inv_gamma = st->inv_gamma;
+    // Steps 3 and 4: t_{k+1} and the extrapolation coefficient, once per CTA (an FP64 square
+    // root and divide per thread would dominate this kernel on GB300's narrow FP64 pipe)
+    __shared__ double s_tb[2];
+    if (threadIdx.x == 0) {
+        const double tk = st->t;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+        s_tb[0] = tn;
+        s_tb[1] = (st->accelerate && !a.init) ? (tk - 1.0) / tn : 0.0;
+    }
     const PT *rowp = reinterpret_cast<const PT *>(a.rowpart);
     const PT *colp = reinterpret_cast<const PT *>(a.colpart);
     const int W = a.NP + 1;
@@ -58,30 +90,24 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
     s_c[ty][tx] = c;
     if (ty == 0) {
         double r = 0.0;
-        if (valid && !a.init)
-            for (int sp = 0; sp < a.col_splits; ++sp) r += (double)rowp[((long long)sp * a.N + l) * W + a.NP];
+        if (valid && !a.init) r = split_sum<PT>(rowp, a.col_splits, a.N, l, W, a.NP);
         s_r[tx] = r;
     }
     __syncthreads();
     const double r = s_r[tx];
-    double cc = 0.0;
-#pragma unroll
-    for (int y = 0; y < kFY; ++y) cc += s_c[y][tx];
-    const double al = cc - r;
+    const double tn = s_tb[0], beta = s_tb[1], opb = 1.0 + beta;
     // b_l = r_l x_l - sum_j lambda_lj x_j, and Step 1 of the next iteration:
     // C^T lambda~^{k+1} = (1 + beta) C^T lambda^k - beta C^T lambda^{k-1}; xi = b~ / gamma
     double upart = 0.0, bpart = 0.0;
     if (valid) {
         for (int k = ty; k < a.n; k += kFY) {
-            double Bk = 0.0;
-            if (!a.init)
-                for (int sp = 0; sp < a.col_splits; ++sp) Bk += (double)rowp[((long long)sp * a.N + l) * W + k];
+            const double Bk = a.init ? 0.0 : split_sum<PT>(rowp, a.col_splits, a.N, l, W, k);
             const double xk = a.X[(long long)l * a.n + k];
             const double bl = r * xk - Bk;
             a.b_new[(long long)l * a.n + k] = bl;
             bpart += bl * bl;
-            const double bt = (1.0 + beta) * bl - beta * a.b_old[(long long)l * a.n + k];
-            const double xi = bt / gamma;
+            const double bt = opb * bl - beta * a.b_old[(long long)l * a.n + k];
+            const double xi = bt * inv_gamma;
             if (a.precision == CR_FP64) {
                 a.xiT64[(long long)k * a.ldv + l] = xi;
                 upart -= xi * xk;
@@ -102,8 +128,12 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
     __syncthreads();
     double saa = 0.0, say = 0.0, sbb = 0.0;
     if (ty == 0 && valid) {
+        double cc = 0.0;
+#pragma unroll
+        for (int y = 0; y < kFY; ++y) cc += s_c[y][tx];
+        const double al = cc - r;
         a.a_new[l] = al;
-        const double at = (1.0 + beta) * al - beta * a.a_old[l];
+        const double at = opb * al - beta * a.a_old[l];
         const double y = a.ybar[l] + at;
         double u = y;
 #pragma unroll
@@ -181,7 +211,7 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         lp[2] = lg;
         st->k = k;
         st->t = tn;
-        st->beta = st->accelerate ? (tk - 1.0) / tn : 0.0;
+        st->beta = beta;
         st->fin_counter = 0u;
         __threadfence();
     }

@@ -39,6 +39,7 @@ struct DevState {
     double cert_P, cert_infeas_sq;       // last certificate
     int accelerate;
     int err;            // CR_ETIMEOUT when a bounded device-side wait ran out
+    double inv_gamma;   // 1 / gamma (the finalize multiplies; GB300's FP64 divide is costly)
 };
 
 inline int bucket_np(int n) {
