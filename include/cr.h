@@ -66,6 +66,16 @@ typedef enum {
 
 #define CR_MAX_N 32      /* largest point dimension n supported by the kernels */
 
+/* Step size of Step 2 of Figure "papg".
+ *   CR_STEP_CONSTANT: 1/L every iteration.
+ *   CR_STEP_ADAPTIVE: the adaptive rule of Section 4 ("Adaptive Step Size Strategy"): iteration k
+ *     tries s_k = s_{k-1} upsilon^(l-1) for l = 0, 1, ... and keeps the first step 1/s_k that
+ *     satisfies Eq. (adaptive-check); s_0 = L.  Every candidate is one sweep over all pairs; the
+ *     decision is taken on the device (three multiplier buffers instead of two), so cr_dual_step
+ *     counts candidates (sweeps) and cr_gap_info.k counts accepted iterations.  Supported with
+ *     CR_FP64 and CR_MIXED_TF32 (single instances). */
+typedef enum cr_step_rule { CR_STEP_CONSTANT = 0, CR_STEP_ADAPTIVE = 1 } cr_step_rule;
+
 typedef struct cr_options {
     double gamma;        /* Tikhonov parameter gamma > 0 (Section 5 uses 1e-4) */
     double lipschitz;    /* 0: computed on the device at cr_create; > 0: used as L */
@@ -76,6 +86,8 @@ typedef struct cr_options {
     int graph_iters;     /* iterations per captured CUDA graph in cr_dual_step (even; 0: no graphs) */
     int tile_cols;       /* columns of Lambda per work item (multiple of 128; 0: chosen by the library) */
     int deterministic;   /* kept for ABI stability: every reduction is already in a fixed order */
+    int step_rule;       /* cr_step_rule: CR_STEP_CONSTANT (1/L, Figure "papg") or CR_STEP_ADAPTIVE */
+    double upsilon;      /* CR_STEP_ADAPTIVE: the factor upsilon > 1 of the step rule (default 2) */
 } cr_options;
 
 /* Convergence record for eta(lambda^k), the primal of Theorem "rate". */
@@ -88,10 +100,13 @@ typedef struct cr_gap_info {
     double rel_gap;      /* max(|lagr_gap| / primal_r, infeas_norm / rms(ybar)) */
     double cert_primal;  /* r_gamma of the feasible max-affine repair of eta(lambda^k): >= p*_gamma */
     double cert_gap_rel; /* (cert_primal - dual_g) / cert_primal: a certified bound on (p* - g)/p* */
+    double step;         /* 1/s of the next candidate step (1/L with CR_STEP_CONSTANT) */
+    long long sweeps;    /* sweeps over all pairs so far (= k with CR_STEP_CONSTANT) */
 } cr_gap_info;
 
 /* Fills *opt with the defaults: gamma 1e-4, lipschitz 0 (computed), CR_L_HESSIAN,
- * CR_FP32, accelerate 1, check_every 100, graph_iters 32, tile_cols 0. */
+ * CR_FP32, accelerate 1, check_every 100, graph_iters 32, tile_cols 0, CR_STEP_CONSTANT,
+ * upsilon 2. */
 CR_API void cr_default_options(cr_options *opt);
 
 /* Creates a solver for one instance (Eq. (regularize)).

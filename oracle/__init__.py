@@ -58,6 +58,8 @@ def _load():
             lib.cro_dual_obj.restype = d
             lib.cro_papg.argtypes = [i, i, _dp, _dp, d, d, i, i, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.cro_papg.restype = i
+            lib.cro_papg_adaptive.argtypes = [i, i, _dp, _dp, d, d, d, i, i, _dp, _dp, _dp, _dp, _ip, _dp]
+            lib.cro_papg_adaptive.restype = i
             lib.cro_certify.argtypes = [i, i, _dp, _dp, d, _dp, _dp, _dp, _ip, _dp]
             lib.cro_threads.restype = i
             _lib = lib
@@ -132,9 +134,15 @@ class PAPG:
     """State of the oracle iteration: (theta^{k-1}, theta~^k, t_k, k).
 
     ``step(iters)`` runs Figure "papg" (K = N) and returns per-iteration logs of
-    g_gamma(theta^k), r_gamma(eta(theta^k)) and <theta^k, C eta(theta^k)>."""
+    g_gamma(theta^k), r_gamma(eta(theta^k)) and <theta^k, C eta(theta^k)>.  With
+    ``adaptive=True`` Step 2 uses the adaptive step size of Section 4 (Eq. (adaptive-check),
+    s_k = s_{k-1} upsilon^(l_k - 1), s_0 = L); the log then holds g and the trial counts."""
 
-    def __init__(self, X, ybar, gamma, L, accel=True, theta0=None):
+    def __init__(self, X, ybar, gamma, L, accel=True, theta0=None, adaptive=False, upsilon=2.0):
+        self.adaptive = bool(adaptive)
+        self.upsilon = float(upsilon)
+        self.s = np.array([float(L)])    # s_0 = L (adaptive step rule)
+        self.trials = []
         self.X = _f64(X)
         self.ybar = _f64(ybar)
         self.N, self.n = self.X.shape
@@ -149,6 +157,19 @@ class PAPG:
 
     def step(self, iters=1, log=True):
         N, n = self.N, self.n
+        if self.adaptive:
+            tr = np.empty(iters, dtype=np.int32)
+            lg_ = np.empty(iters) if log else None
+            rc = _load().cro_papg_adaptive(N, n, _p(self.X), _p(self.ybar), self.gamma, self.L, self.upsilon,
+                                           int(iters), int(self.accel), _p(self.theta), _p(self.theta_tilde),
+                                           _p(self.t), _p(self.s), tr.ctypes.data_as(_ip), _p(lg_))
+            if rc == -1:
+                raise MemoryError("oracle iteration could not allocate its work arrays")
+            if rc == -2:
+                raise FloatingPointError("no step passed the adaptive check")
+            self.k += iters
+            self.trials.extend(int(v) for v in tr)
+            return dict(g=lg_, trials=tr) if log else None
         lg_ = np.empty(iters) if log else None
         lr_ = np.empty(iters) if log else None
         ll_ = np.empty(iters) if log else None

@@ -198,6 +198,104 @@ int cro_papg(int N, int n, const double *X, const double *ybar, double gamma, do
 }
 
 /*
+ * P-APG with the adaptive step size of Section 4 ("Adaptive Step Size Strategy"),
+ * taking `iters` iterations from the state (theta^{k-1}, theta~^k, t_k, s_{k-1}):
+ * iteration k tries s_k = s_{k-1} * upsilon^(l - 1) for l = 0, 1, 2, ... and keeps the
+ * first l for which Eq. (adaptive-check)
+ *     g(theta^k) >= g(theta~^k) + <grad g(theta~^k), theta^k - theta~^k>
+ *                   - (s_k / 2) ||theta^k - theta~^k||^2
+ * holds, where theta^k = (theta~^k - C eta^k / s_k)_+ (Step 2 with 1/s_k for 1/L);
+ * s_0 = L_gamma (the caller's initial *s).  Steps 1, 3 and 4 are those of Figure "papg".
+ * g_gamma is a concave quadratic (Eq. (g_gamma) at eta(theta) is
+ * -1/2||a||^2 - a.ybar - ||b||^2/(2 gamma) with (a, b) = C^T theta), so for D = theta^k - theta~^k
+ * the check is exactly
+ *     ||da||^2 + ||db||^2 / gamma <= s_k ||D||^2,   (da, db) = C^T D,
+ * and s_k never exceeds L: Section 4 allows any s_k <= L_gamma, and at s_k = L (a bound on
+ * the curvature of g_gamma) the check holds in exact arithmetic, so that candidate is kept
+ * (rounding cannot push the step below the constant one).
+ * which is how it is evaluated here (C^T applied to D over all pairs): the literal form
+ * subtracts nearly equal objective values once the steps are small.  A test pins the
+ * identity against the literal form.
+ * In/out: th_prev, th_tilde, *t as in cro_papg; *s: s_{k-1} -> s_{k-1+iters}.
+ * trials (length iters, may be NULL): l_k + 1, the candidate steps of each iteration.
+ * log_g (may be NULL): g(theta^k).  Returns 0, -1 on allocation failure, -2 when no step
+ * passes within 200 trials (non-finite data).
+ */
+int cro_papg_adaptive(int N, int n, const double *X, const double *ybar, double gamma,
+                      double L, double upsilon, int iters, int accel, double *th_prev,
+                      double *th_tilde, double *t, double *s, int *trials, double *log_g)
+{
+    size_t NN = (size_t)N * N;
+    double *y = (double *)malloc((size_t)N * sizeof(double));
+    double *xi = (double *)malloc((size_t)N * n * sizeof(double));
+    double *ceta = (double *)malloc(NN * sizeof(double));
+    double *th_new = (double *)malloc(NN * sizeof(double));
+    double *dif = (double *)malloc(NN * sizeof(double));
+    double *da = (double *)malloc((size_t)N * sizeof(double));
+    double *db = (double *)malloc((size_t)N * n * sizeof(double));
+    if (!y || !xi || !ceta || !th_new || !dif || !da || !db) {
+        free(y); free(xi); free(ceta); free(th_new); free(dif); free(da); free(db);
+        return -1;
+    }
+    int rc = 0;
+    for (int it = 0; it < iters && rc == 0; ++it) {
+        /* Step 1 at theta~^k */
+        cro_eta_of_theta(N, n, X, ybar, gamma, th_tilde, y, xi);
+        cro_c_apply(N, n, X, y, xi, ceta);
+        double sk = *s / upsilon;  /* l = 0 */
+        int l = 0;
+        for (;;) {
+            /* Step 2 with step 1/s_k */
+#pragma omp parallel for schedule(static)
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    double v = 0.0;
+                    if (i != j) {
+                        v = th_tilde[IDX(i, j, N)] - ceta[IDX(i, j, N)] / sk;
+                        if (v < 0.0) v = 0.0;
+                    }
+                    th_new[IDX(i, j, N)] = v;
+                    dif[IDX(i, j, N)] = v - th_tilde[IDX(i, j, N)];
+                }
+            /* Eq. (adaptive-check) */
+            cro_ct_apply(N, n, X, dif, da, db);
+            double lhs = 0.0, nn = 0.0;
+            for (int i = 0; i < N; ++i) lhs += da[i] * da[i];
+            double bb = 0.0;
+            for (size_t q = 0; q < (size_t)N * n; ++q) bb += db[q] * db[q];
+            lhs += bb / gamma;
+            for (int i = 0; i < N; ++i) {
+                double nni = 0.0;
+                for (int j = 0; j < N; ++j) nni += dif[IDX(i, j, N)] * dif[IDX(i, j, N)];
+                nn += nni;
+            }
+            if (lhs <= sk * nn || sk >= L) break;  /* s_k = L always qualifies (s_k <= L allowed) */
+            if (++l >= 200) {
+                rc = -2;
+                break;
+            }
+            sk = sk * upsilon < L ? sk * upsilon : L;
+        }
+        if (rc) break;
+        if (trials) trials[it] = l + 1;
+        *s = sk;
+        /* Steps 3 and 4 */
+        const double tk = *t;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+        const double beta = accel ? (tk - 1.0) / tn : 0.0;
+#pragma omp parallel for schedule(static)
+        for (long long q = 0; q < (long long)NN; ++q) {
+            th_tilde[q] = th_new[q] + beta * (th_new[q] - th_prev[q]);
+            th_prev[q] = th_new[q];
+        }
+        *t = tn;
+        if (log_g) log_g[it] = cro_dual_obj(N, n, X, ybar, gamma, th_prev, ceta, NULL, NULL, NULL, NULL);
+    }
+    free(y); free(xi); free(ceta); free(th_new); free(dif); free(da); free(db);
+    return rc;
+}
+
+/*
  * Certified upper bound on p*_gamma from any (y, xi): the convex piecewise-linear
  * function f(x) = max_i ( y_i + xi_i . (x - x_i) ) is evaluated at every x_j;
  * y_rep_j = f(x_j) and xi_rep_j = xi_{m(j)} for a maximising piece m(j) form a

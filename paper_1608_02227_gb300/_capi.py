@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcrgb.so")
 CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ENUMERIC, CR_EUNSUPPORTED = range(8)
 CR_FP64, CR_FP32, CR_MIXED_TF32 = 0, 1, 2
 CR_L_HESSIAN, CR_L_PAPER = 0, 1
+CR_STEP_CONSTANT, CR_STEP_ADAPTIVE = 0, 1
 CR_MAX_N = 32
 
 
@@ -29,6 +30,8 @@ class cr_options(ctypes.Structure):
         ("graph_iters", ctypes.c_int),
         ("tile_cols", ctypes.c_int),
         ("deterministic", ctypes.c_int),
+        ("step_rule", ctypes.c_int),
+        ("upsilon", ctypes.c_double),
     ]
 
 
@@ -42,6 +45,8 @@ class cr_gap_info(ctypes.Structure):
         ("rel_gap", ctypes.c_double),
         ("cert_primal", ctypes.c_double),
         ("cert_gap_rel", ctypes.c_double),
+        ("step", ctypes.c_double),
+        ("sweeps", ctypes.c_longlong),
     ]
 
     def as_dict(self):

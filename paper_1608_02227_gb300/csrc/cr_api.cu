@@ -82,6 +82,9 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.st = c->st;
         a.rowpart = (double *)c->rowpart;
         a.colpart = (double *)c->colpart;
+        a.adaptive = c->adaptive ? 1 : 0;
+        for (int i = 0; i < 3; ++i) a.B[i] = (double *)c->lam[i];
+        a.dpart = (double *)c->dpart;
         CR_CUDA(launch_sweep_d(c->NP, a, c->grid, c->stream));
     } else if (c->tc) {
         TcSweepArgs a{};
@@ -99,11 +102,12 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.rowpart = (float *)c->rowpart;
         a.colpart = (float *)c->colpart;
         a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
-        TcMaps m = c->tcm;
-        m.P = &c->tc_lam[P];
-        m.Q = &c->tc_lam[Q];
-        m.Qs = &c->tc_lam32[Q];
-        CR_CUDA(launch_sweep_tc(m, a, c->grid, c->stream));
+        a.lmaps = c->tc_ld;
+        a.smaps = c->tc_st;
+        a.p_host = P;
+        a.adaptive = c->adaptive ? 1 : 0;
+        a.dpart = (float *)c->dpart;
+        CR_CUDA(launch_sweep_tc(c->tcm, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
         a.Q = (float *)c->lam[Q];
@@ -173,7 +177,19 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
     f.log = c->log;
     f.st = c->st;
     f.init = 0;
+    if (c->adaptive) {  // pass 1 decides on the device; the roles of the buffers follow from it
+        f.adaptive = 1;
+        f.a_new = c->ha_c;
+        f.b_new = c->hb_c;
+        for (int i = 0; i < 2; ++i) {
+            f.hist_a[i] = c->ha[i];
+            f.hist_b[i] = c->hb[i];
+        }
+        f.dpart = c->dpart;
+        f.dgroups = c->dgroups;
+    }
     CR_CUDA(launch_finalize(f, c->stream));
+    if (c->adaptive) CR_CUDA(launch_commit(f, c->stream));
     return CR_OK;
 }
 
@@ -324,9 +340,10 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         return CR_ENUMERIC;
     }
 
-    // multipliers: lambda^0 = lambda^{-1} = 0
+    // multipliers: lambda^0 = lambda^{-1} = 0 (and a zeroed third buffer for the adaptive step)
     const size_t lam_count = (size_t)N * c->ld;
-    for (int i = 0; i < 2; ++i) {
+    const int nbuf = c->adaptive ? 3 : 2;
+    for (int i = 0; i < nbuf; ++i) {
         if (f64) {
             double *p;
             CR_TRY(dev_alloc(c, &p, lam_count));
@@ -337,10 +354,26 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
             c->lam[i] = p;
         }
         CR_CUDA(cudaMemsetAsync(c->lam[i], 0, lam_count * tsz, c->stream));
+    }
+    for (int i = 0; i < 2; ++i) {
         CR_TRY(dev_alloc(c, &c->ha[i], (size_t)N));
         CR_TRY(dev_alloc(c, &c->hb[i], (size_t)N * n));
         CR_CUDA(cudaMemsetAsync(c->ha[i], 0, sizeof(double) * N, c->stream));
         CR_CUDA(cudaMemsetAsync(c->hb[i], 0, sizeof(double) * N * n, c->stream));
+    }
+    if (c->adaptive) {
+        CR_TRY(dev_alloc(c, &c->ha_c, (size_t)N));
+        CR_TRY(dev_alloc(c, &c->hb_c, (size_t)N * n));
+        c->dgroups = c->S * (c->tc ? 2 : 1);
+        if (f64) {
+            double *p;
+            CR_TRY(dev_alloc(c, &p, (size_t)c->dgroups * N));
+            c->dpart = p;
+        } else {
+            float *p;
+            CR_TRY(dev_alloc(c, &p, (size_t)c->dgroups * N));
+            c->dpart = p;
+        }
     }
     if (c->tc) {
         const size_t rm = (size_t)c->ldv * 32;
@@ -349,10 +382,17 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_TRY(dev_alloc(c, &c->xi_rm, 2 * rm));
         CR_CUDA(cudaMemsetAsync(c->xi_rm, 0, 2 * rm * sizeof(float), c->stream));
         CR_CUDA(launch_tc_points(c->X, N, n, c->ldv, c->xr, c->xt, c->stream));
-        for (int i = 0; i < 2; ++i)
-            CR_CUDA(make_tmap_2d(&c->tc_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
-        for (int i = 0; i < 2; ++i)
-            CR_CUDA(make_tmap_2d(&c->tc_lam32[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 32, true));
+        CUtensorMap hl[3], hs[3];
+        memset(hl, 0, sizeof(hl));
+        memset(hs, 0, sizeof(hs));
+        for (int i = 0; i < nbuf; ++i) {
+            CR_CUDA(make_tmap_2d(&hl[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
+            CR_CUDA(make_tmap_2d(&hs[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 32, true));
+        }
+        CR_TRY(dev_alloc(c, &c->tc_ld, 3));
+        CR_TRY(dev_alloc(c, &c->tc_st, 3));
+        CR_CUDA(cudaMemcpyAsync(c->tc_ld, hl, sizeof(hl), cudaMemcpyHostToDevice, c->stream));
+        CR_CUDA(cudaMemcpyAsync(c->tc_st, hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
         CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));
@@ -381,7 +421,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         c->colpart = b;
     }
     const int gN = (N + 255) / 256;
-    CR_TRY(dev_alloc(c, &c->finblk, (size_t)finalize_blocks(N) * 3));
+    CR_TRY(dev_alloc(c, &c->finblk, (size_t)finalize_blocks(N) * 6));
     CR_TRY(dev_alloc(c, &c->certblk, (size_t)gN * 2));
     CR_TRY(dev_alloc(c, &c->log, (size_t)kLogCap * 3));
     CR_TRY(dev_alloc(c, &c->st, 1));
@@ -402,6 +442,13 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     h.inv_gamma = 1.0 / c->opt.gamma;
     h.k = 0;
     h.accelerate = c->opt.accelerate ? 1 : 0;
+    if (c->adaptive) {  // the first candidate tries s_1 = s_0 / upsilon with s_0 = L
+        h.adaptive = 1;
+        h.ring = 0;
+        h.upsilon = c->opt.upsilon;
+        h.inv_L = 1.0 / c->L;
+        h.s = c->opt.upsilon / c->L;
+    }
     CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
 
     // eta(lambda~^1) = eta(lambda^0) = (ybar, 0)
@@ -441,8 +488,26 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     return CR_OK;
 }
 
+// The accepted iteration count and the buffer holding lambda^k: host-side with the constant
+// step, from the device state with the adaptive one (its accept/reject runs on the device).
+cr_status current_k(const cr_ctx *c, long long *k, int *lam_buf) {
+    if (!c->adaptive) {
+        *k = c->k;
+        *lam_buf = (int)(c->k & 1);
+        return CR_OK;
+    }
+    DevState h{};
+    CR_TRY(fetch_state(c, &h));
+    *k = h.k;
+    *lam_buf = h.ring;
+    return CR_OK;
+}
+
 // Enqueues the pass over all pairs for eta(lambda^k) (certificate + infeasibility).
 cr_status gap_launch(cr_ctx *c) {
+    long long kk = 0;
+    int lb = 0;
+    CR_TRY(current_k(c, &kk, &lb));
     CertArgs a{};
     a.N = c->N;
     a.n = c->n;
@@ -452,8 +517,8 @@ cr_status gap_launch(cr_ctx *c) {
     a.ldv = c->ldv;
     a.X = c->X;
     a.ybar = c->ybar;
-    a.a = c->ha[c->k & 1];
-    a.b = c->hb[c->k & 1];
+    a.a = c->ha[kk & 1];
+    a.b = c->hb[kk & 1];
     a.yh = c->c_yh;
     a.yl = c->c_yl;
     a.uh = c->c_uh;
@@ -495,6 +560,8 @@ cr_status gap_finish(const cr_ctx *c, DevState h, cr_gap_info *out) {
     g.rel_gap = std::max(fabs(g.lagr_gap) / rden, g.infeas_norm / c->ybar_rms);
     g.cert_primal = h.cert_P;
     g.cert_gap_rel = (h.cert_P - h.last_g) / (fabs(h.cert_P) > 1e-300 ? fabs(h.cert_P) : 1e-300);
+    g.step = h.s;
+    g.sweeps = c->adaptive ? h.sweeps : h.k;
     if (out) *out = g;
     if (!isfinite(g.dual_g) || !isfinite(g.primal_r) || !isfinite(g.cert_primal)) {
         set_err("non-finite objective at k = %lld", h.k);
@@ -521,6 +588,8 @@ CR_API void cr_default_options(cr_options *o) {
     o->graph_iters = 32;
     o->tile_cols = 0;
     o->deterministic = 1;
+    o->step_rule = CR_STEP_CONSTANT;
+    o->upsilon = 2.0;
 }
 
 CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int n, const cr_options *opt,
@@ -563,6 +632,20 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
         set_err("lipschitz must be finite and >= 0");
         return CR_EINVAL;
     }
+    if (o.step_rule != CR_STEP_CONSTANT && o.step_rule != CR_STEP_ADAPTIVE) {
+        set_err("unknown step rule %d", o.step_rule);
+        return CR_EINVAL;
+    }
+    if (o.step_rule == CR_STEP_ADAPTIVE) {
+        if (!(o.upsilon > 1.0) || !isfinite(o.upsilon)) {
+            set_err("upsilon must be finite and > 1");
+            return CR_EINVAL;
+        }
+        if (o.precision == CR_FP32) {
+            set_err("the adaptive step runs with CR_FP64 or CR_MIXED_TF32");
+            return CR_EUNSUPPORTED;
+        }
+    }
     if (o.check_every < 1) o.check_every = 1;
     if (o.graph_iters < 0 || (o.graph_iters & 1)) {
         set_err("graph_iters must be even and >= 0");
@@ -580,6 +663,7 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
     c->N = (int)N;
     c->n = n;
     c->opt = o;
+    c->adaptive = o.step_rule == CR_STEP_ADAPTIVE;
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -707,7 +791,10 @@ CR_API cr_status cr_primal(const cr_ctx *c, double *y, double *xi) {
         set_err("ctx is NULL");
         return CR_EINVAL;
     }
-    CR_CUDA(launch_primal(c->N, c->n, c->ybar, c->ha[c->k & 1], c->hb[c->k & 1], c->st, c->tmp_y, c->tmp_xi,
+    long long kk = 0;
+    int lb = 0;
+    CR_TRY(current_k(c, &kk, &lb));
+    CR_CUDA(launch_primal(c->N, c->n, c->ybar, c->ha[kk & 1], c->hb[kk & 1], c->st, c->tmp_y, c->tmp_xi,
                           c->stream));
     if (y) CR_CUDA(cudaMemcpyAsync(y, c->tmp_y, sizeof(double) * c->N, cudaMemcpyDefault, c->stream));
     if (xi)
@@ -722,7 +809,10 @@ CR_API cr_status cr_lambda(const cr_ctx *c, long long row0, long long rows, doub
         return CR_EINVAL;
     }
     if (rows == 0) return CR_OK;
-    const void *lam = c->lam[c->k & 1];  // lambda^k lives in lam[k & 1] (lam[0] = lambda^0 at k = 0)
+    long long kk = 0;
+    int lb = 0;
+    CR_TRY(current_k(c, &kk, &lb));
+    const void *lam = c->lam[lb];  // constant step: lambda^k lives in lam[k & 1] (lam[0] = lambda^0 at k = 0)
     cudaPointerAttributes at{};
     bool dev = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
                (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
@@ -776,9 +866,10 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              "\"row_blocks\": %d, \"col_splits\": %d, \"cols_per_split\": %d, \"grid\": %d, "
              "\"ctas_per_sm\": %d, \"sms\": %d, \"pairs\": %.0f, \"lambda_bytes_per_iter\": %.0f, "
              "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d, "
-             "\"sweep\": \"%s\"}",
+             "\"step_rule\": %d, \"upsilon\": %.17g, \"sweep\": \"%s\"}",
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
-             pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters,
+             pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters, c->opt.step_rule,
+             c->opt.upsilon,
              c->tc ? "tcgen05" : (c->tma ? "tma" : (is_f64(c) ? "fp64" : "simple")));
     return CR_OK;
 }

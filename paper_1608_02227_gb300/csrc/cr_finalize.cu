@@ -222,6 +222,207 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_kernel(const FinArgs a) {
     finalize_body<PT>(a, blockIdx.x, gridDim.x);
 }
 
+// Adaptive step size (Section 4), pass 1 of an iteration: C^T of the candidate lambda^k,
+// the terms of Eq. (adaptive-check), g_gamma(lambda^k), and the accept/reject decision.
+// g_gamma is quadratic, so g(l) - g(l~) - <grad g(l~), l - l~> = -1/2 (||da||^2 + ||db||^2/gamma)
+// with (da, db) = C^T (l - l~) = (a,b)^k - (a~,b~) (linearity), and the check reads
+//     ||da||^2 + ||db||^2 / gamma  <=  s_k ||lambda^k - lambda~^k||^2,
+// the last norm summed over all pairs by the sweep.  Accepted: k, t, beta, the log advance,
+// the buffer roles rotate and the next candidate tries s_{k+1} = s_k / upsilon; rejected:
+// the same sweep runs again with min(s_k * upsilon, L).  Fixed-order reductions throughout.
+template <typename PT>
+__device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int blk, const int nblk) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int l = blk * kFX + tx;
+    const bool valid = l < a.N;
+    DevState *st = a.st;
+    __shared__ long long s_k;
+    __shared__ double s_bo;
+    if (threadIdx.x == 0) {
+        s_k = st->k + 1;  // index of the iteration being tried
+        s_bo = st->beta;  // beta of lambda~^k
+    }
+    const PT *rowp = reinterpret_cast<const PT *>(a.rowpart);
+    const PT *colp = reinterpret_cast<const PT *>(a.colpart);
+    const int W = a.NP + 1;
+    __shared__ double s_c[kFY][kFX], s_u[kFY][kFX], s_b[kFY][kFX];
+    __shared__ double s_r[kFX];
+    double c = 0.0;
+    if (valid) {
+        int b = ty;
+        for (; b + 7 * kFY < a.row_blocks; b += 8 * kFY) {
+            PT v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = colp[(long long)(b + u * kFY) * a.ld + l];
+            c += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+        }
+        for (; b < a.row_blocks; b += kFY) c += (double)colp[(long long)b * a.ld + l];
+    }
+    s_c[ty][tx] = c;
+    if (ty == 0) s_r[tx] = valid ? split_sum<PT>(rowp, a.col_splits, a.N, l, W, a.NP) : 0.0;
+    __syncthreads();
+    const double r = s_r[tx];
+    const long long k = s_k;
+    const double bo = s_bo, opbo = 1.0 + bo;
+    const double *a1 = a.hist_a[(k - 1) & 1], *a2 = a.hist_a[k & 1];
+    const double *b1 = a.hist_b[(k - 1) & 1], *b2 = a.hist_b[k & 1];
+    double bpart = 0.0, dbpart = 0.0;
+    if (valid) {
+        for (int kk = ty; kk < a.n; kk += kFY) {
+            const long long o = (long long)l * a.n + kk;
+            const double bl = r * a.X[o] - split_sum<PT>(rowp, a.col_splits, a.N, l, W, kk);
+            a.b_new[o] = bl;
+            bpart += bl * bl;
+            const double db = bl - (opbo * b1[o] - bo * b2[o]);  // b^k - b~ of lambda~^k
+            dbpart += db * db;
+        }
+    }
+    s_u[ty][tx] = dbpart;
+    s_b[ty][tx] = bpart;
+    __syncthreads();
+    double v6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // ||a||^2, a.ybar, ||b||^2, ||da||^2, ||db||^2, ||dl||^2
+    if (ty == 0 && valid) {
+        double cc = 0.0, bb = 0.0, dbb = 0.0;
+#pragma unroll
+        for (int y = 0; y < kFY; ++y) {
+            cc += s_c[y][tx];
+            bb += s_b[y][tx];
+            dbb += s_u[y][tx];
+        }
+        const double al = cc - r;
+        a.a_new[l] = al;
+        const double da = al - (opbo * a1[l] - bo * a2[l]);
+        const PT *dp = reinterpret_cast<const PT *>(a.dpart);
+        double dl = 0.0;
+        for (int g = 0; g < a.dgroups; ++g) dl += (double)dp[(long long)g * a.N + l];
+        v6[0] = al * al;
+        v6[1] = al * a.ybar[l];
+        v6[2] = bb;
+        v6[3] = da * da;
+        v6[4] = dbb;
+        v6[5] = dl;
+    }
+    __shared__ bool last;
+    if (ty == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v6[q] += __shfl_xor_sync(0xffffffffu, v6[q], o);
+        if (tx == 0) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) a.blockpart[blk * 6 + q] = v6[q];
+            __threadfence();
+            const unsigned ticket = atomicAdd(&st->fin_counter, 1u);
+            last = (ticket == (unsigned)nblk - 1u);
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double s_red[6][kFX * kFY];
+    {
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < nblk; b += kFX * kFY)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[q] += __ldcg(a.blockpart + b * 6 + q);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s_red[q][threadIdx.x] = acc[q];
+    }
+    __syncthreads();
+    for (int w = kFX * kFY / 2; w > 0; w >>= 1) {
+        const int t = threadIdx.x;
+        if (t < w)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s_red[q][t] += s_red[q][t + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double gamma = st->gamma, inv_gamma = st->inv_gamma;
+        const double aa = s_red[0][0], ay = s_red[1][0], bb = s_red[2][0];
+        const double lhs = (s_red[3][0] + s_red[4][0] * inv_gamma) * st->s;  // st->s = 1 / s_k
+        const double rhs = s_red[5][0];
+        st->check_lhs = lhs;
+        st->check_rhs = rhs;
+        st->sweeps += 1;
+        // s_k = L satisfies the check in exact arithmetic (L bounds the curvature of g_gamma,
+        // and Section 4 allows any s_k <= L), so a candidate at 1/L is kept: rounding in the
+        // check cannot push the step below the constant one
+        if (lhs <= rhs || st->s <= st->inv_L) {
+            const double g = -0.5 * aa - ay - bb / (2.0 * gamma);
+            const double rr = 0.5 * aa + bb / (2.0 * gamma);
+            const double lg = aa + ay + bb / gamma;
+            st->last_g = g;
+            st->last_r = rr;
+            st->last_lg = lg;
+            double *lp = a.log + (size_t)((k - 1) % kLogCap) * 3;
+            lp[0] = g;
+            lp[1] = rr;
+            lp[2] = lg;
+            const double tk = st->t;
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+            st->k = k;
+            st->t = tn;
+            st->beta = st->accelerate ? (tk - 1.0) / tn : 0.0;
+            st->ring = st->ring == 0 ? 2 : st->ring - 1;  // the candidate becomes lambda^k
+            st->s = st->s * st->upsilon;
+            st->accepted = 1;
+        } else {
+            st->s = fmax(st->s / st->upsilon, st->inv_L);
+            st->accepted = 0;
+        }
+        st->fin_counter = 0u;
+        __threadfence();
+    }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(kFX * kFY) finalize_adapt_kernel(const FinArgs a) {
+    finalize_adapt_body<PT>(a, blockIdx.x, gridDim.x);
+}
+
+// Adaptive step, pass 2 (one thread per point): after an accepted candidate, (a,b)^k takes the
+// history slot of (a,b)^{k-2} and Step 1 of the next iteration builds eta(lambda~^{k+1}) with
+// C^T lambda~^{k+1} = (1 + beta) C^T lambda^k - beta C^T lambda^{k-1}; after a rejected one
+// nothing changes and the next sweep retries from the same lambda~^k.
+__global__ void commit_kernel(const FinArgs a) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const DevState *st = a.st;
+    if (l >= a.N || !st->accepted) return;
+    const long long k = st->k;
+    const double beta = st->beta, opb = 1.0 + beta, inv_gamma = st->inv_gamma;
+    double *a0 = a.hist_a[k & 1], *b0 = a.hist_b[k & 1];
+    const double *a1 = a.hist_a[(k - 1) & 1], *b1 = a.hist_b[(k - 1) & 1];
+    const double al = a.a_new[l];
+    a0[l] = al;
+    const double y = a.ybar[l] + (opb * al - beta * a1[l]);
+    double u = y;
+    for (int kk = 0; kk < a.n; ++kk) {
+        const long long o = (long long)l * a.n + kk;
+        const double bl = a.b_new[o];
+        b0[o] = bl;
+        const double xi = (opb * bl - beta * b1[o]) * inv_gamma;
+        if (a.precision == CR_FP64) {
+            a.xiT64[(long long)kk * a.ldv + l] = xi;
+            u -= xi * a.X[o];
+        } else {
+            const float xf = (float)xi;
+            a.xiT[(long long)kk * a.ldv + l] = xf;
+            if (a.xi_rm) {
+                a.xi_rm[(long long)l * 32 + kk] = xf;
+                a.xi_rm[a.ldv * 32 + (long long)l * 32 + kk] = xf - __uint_as_float(__float_as_uint(xf) & 0xFFFFE000u);
+            }
+            u -= (double)xf * (double)a.xT32[(long long)kk * a.ldv + l];
+        }
+    }
+    if (a.precision == CR_FP64) {
+        a.y64[l] = y;
+        a.u64[l] = u;
+    } else {
+        split_hi_lo(y, a.yh + l, a.yl + l);
+        split_hi_lo(u, a.uh + l, a.ul + l);
+    }
+}
+
 // Batched finalize: one CTA per (instance, 32-point block) of the work-list.
 __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDesc *d, const FinItem *items) {
     const FinItem it = items[blockIdx.x];
@@ -325,10 +526,21 @@ cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int n
 
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s) {
     const unsigned g = blocks_for(a.N, kFX);
-    if (a.precision == CR_FP64)
+    if (a.adaptive) {
+        if (a.precision == CR_FP64)
+            finalize_adapt_kernel<double><<<g, kFX * kFY, 0, s>>>(a);
+        else
+            finalize_adapt_kernel<float><<<g, kFX * kFY, 0, s>>>(a);
+    } else if (a.precision == CR_FP64) {
         finalize_kernel<double><<<g, kFX * kFY, 0, s>>>(a);
-    else
+    } else {
         finalize_kernel<float><<<g, kFX * kFY, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const FinArgs &a, cudaStream_t s) {
+    commit_kernel<<<blocks_for(a.N, 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,11 @@ struct cr_ctx {
     double *X = nullptr, *ybar = nullptr;
     float *xT32 = nullptr;
     double *xT64 = nullptr;
-    void *lam[2] = {nullptr, nullptr};
+    void *lam[3] = {nullptr, nullptr, nullptr};  // the third only with the adaptive step
+    bool adaptive = false;       // CR_STEP_ADAPTIVE
+    double *ha_c = nullptr, *hb_c = nullptr;    // adaptive: C^T of the candidate
+    void *dpart = nullptr;       // adaptive: row sums of (lambda^k - lambda~^k)^2 per split (and group)
+    int dgroups = 0;
     double *ha[2] = {nullptr, nullptr}, *hb[2] = {nullptr, nullptr};
     float *yh = nullptr, *yl = nullptr, *uh = nullptr, *ul = nullptr, *xiT = nullptr;
     double *y64 = nullptr, *u64 = nullptr, *xiT64 = nullptr;
@@ -45,7 +49,7 @@ struct cr_ctx {
     CUtensorMap tm_lam[2];
     TmaMaps tm{};
     bool tc = false;             // CR_MIXED_TF32: tensor-core sweep (cr_sweep_tc.cu)
-    CUtensorMap tc_lam[2], tc_lam32[2];
+    CUtensorMap *tc_ld = nullptr, *tc_st = nullptr;  // device arrays: load / store maps of the buffers
     TcMaps tcm{};
     float *xr = nullptr, *xt = nullptr, *xi_rm = nullptr;
     // graph of graph_iters iterations starting at an even k

@@ -40,7 +40,31 @@ struct DevState {
     int accelerate;
     int err;            // CR_ETIMEOUT when a bounded device-side wait ran out
     double inv_gamma;   // 1 / gamma (the finalize multiplies; GB300's FP64 divide is costly)
+    // adaptive step size (Section 4, Eq. (adaptive-check)); s above is 1/s_k of the next candidate
+    int adaptive;       // 1: three multiplier buffers, accept/reject decided on the device
+    int ring;           // lambda^{k-1} is buffer ring, lambda^{k-2} ring+1, the candidate ring+2 (mod 3)
+    int accepted;       // the last candidate passed the check
+    double upsilon;     // step factor
+    double inv_L;       // 1/L: the step never drops below it, and a candidate at 1/L is always kept
+    long long sweeps;   // candidate steps taken
+    double check_lhs, check_rhs;  // last check: (||da||^2 + ||db||^2/gamma)/s_k <= ||lambda^k - lambda~^k||^2
 };
+
+// Roles of the multiplier buffers in the sweep about to run: inputs lambda^{k-1} (p),
+// lambda^{k-2} (q), output (r).  Constant step: two buffers, the caller's parity p_host and
+// r = q.  Adaptive step: three buffers rotated on the device (accept: ring += 2 mod 3).
+__device__ __forceinline__ void lam_roles(const DevState *st, int adaptive, int p_host, int *p, int *q, int *r) {
+    if (adaptive) {
+        const int rr = st->ring;
+        *p = rr;
+        *q = rr == 2 ? 0 : rr + 1;
+        *r = rr == 0 ? 2 : rr - 1;
+    } else {
+        *p = p_host;
+        *q = p_host ^ 1;
+        *r = *q;
+    }
+}
 
 inline int bucket_np(int n) {
     static const int b[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
@@ -73,6 +97,9 @@ struct SweepArgsF {
 struct SweepArgsD {
     const double *P;
     double *Q;
+    double *B[3];            // adaptive step: the three multiplier buffers (roles from DevState)
+    int adaptive;
+    double *dpart;           // adaptive step: S x N row sums of (lambda^k - lambda~^k)^2
     long long ld;
     int N;
     int row_blocks;
@@ -137,10 +164,13 @@ struct TcSweepArgs {
     float *rowpart;          // S x N x (NP+1)
     float *colpart;          // RB x ld (128-row blocks)
     int *err;
+    const CUtensorMap *lmaps;  // device array: load maps of the multiplier buffers (box 32 x 128)
+    const CUtensorMap *smaps;  // device array: store maps of the same buffers (box 32 x 32)
+    int p_host;              // constant step: buffer holding lambda^{k-1}
+    int adaptive;
+    float *dpart;            // adaptive step: [S][2][N] row sums of (lambda^k - lambda~^k)^2 per epilogue group
 };
 struct TcMaps {
-    const CUtensorMap *P, *Q;            // lambda buffers [N][ld], box 32 x 128, 128-byte swizzle
-    const CUtensorMap *Qs;               // the lambda^k buffer with a 32 x 32 box (per-warp stores)
     CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 64, swizzle
     CUtensorMap XT;                      // points transposed, hi rows (with the ones row) then lo rows [64][ldv], box 32 x 64, swizzle
     CUtensorMap Y;                       // y hi / lo [2][ldv], box 32 x 2
@@ -200,8 +230,18 @@ struct FinArgs {
     double *log;             // kLogCap x 3
     DevState *st;
     int init;                // 1: no partials, a = b = 0 (builds eta(lambda^0))
+    // adaptive step: this launch is pass 1 of an iteration.  (a,b)^k goes to a_new/b_new (the
+    // candidate buffers), C^T lambda^{k-1} and C^T lambda^{k-2} are taken from hist_a/hist_b
+    // by the parity of the device-side k, the recovery waits for launch_commit.
+    int adaptive;
+    double *hist_a[2], *hist_b[2];
+    const void *dpart;       // float or double, dgroups x N: row sums of (lambda^k - lambda~^k)^2
+    int dgroups;
 };
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s);
+// adaptive step, pass 2: when the candidate was accepted, store (a,b)^k in the history and
+// build eta(lambda~^{k+1}) for the next sweep; otherwise nothing changes
+cudaError_t launch_commit(const FinArgs &a, cudaStream_t s);
 int finalize_blocks(int N);   // CTAs of the finalize kernel (size of its block-partial buffer / 3)
 
 // eta(lambda^k) from the history: y = ybar + a, xi = b / gamma (FP64, row-major)

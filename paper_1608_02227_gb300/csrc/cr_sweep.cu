@@ -218,6 +218,16 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
     const double beta = a.st->beta;
     const double s = a.st->s;
     const int items = a.row_blocks * a.col_splits;
+    // buffer roles: lambda^{k-1} (Pp), lambda^{k-2} (Qp), output (Rp)
+    const double *Pp = a.P, *Qp = a.Q;
+    double *Rp = a.Q;
+    if (a.adaptive) {
+        int ip, iq, ir;
+        lam_roles(a.st, 1, 0, &ip, &iq, &ir);
+        Pp = a.B[ip];
+        Qp = a.B[iq];
+        Rp = a.B[ir];
+    }
 
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int rb = item / a.col_splits, sp = item % a.col_splits;
@@ -232,7 +242,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
         }
         int ir[MR];
         bool rv[MR];
-        double ur[MR], rs[MR];
+        double ur[MR], rs[MR], dd[MR];
         double B[MR][NP];
 #pragma unroll
         for (int r = 0; r < MR; ++r) {
@@ -240,6 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
             rv[r] = ir[r] < a.N;
             ur[r] = rv[r] ? a.u[ir[r]] : 0.0;
             rs[r] = 0.0;
+            dd[r] = 0.0;
 #pragma unroll
             for (int k = 0; k < NP; ++k) B[r][k] = 0.0;
         }
@@ -275,8 +286,8 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
             for (int r = 0; r < MR; ++r) {
                 if (rv[r] && cv) {
                     const long long off = (long long)ir[r] * a.ld + jl;
-                    const double2 p01 = ld_stream2(a.P + off), p23 = ld_stream2(a.P + off + 2);
-                    const double2 q01 = ld_stream2(a.Q + off), q23 = ld_stream2(a.Q + off + 2);
+                    const double2 p01 = ld_stream2(Pp + off), p23 = ld_stream2(Pp + off + 2);
+                    const double2 q01 = ld_stream2(Qp + off), q23 = ld_stream2(Qp + off + 2);
                     p4[r][0] = p01.x; p4[r][1] = p01.y; p4[r][2] = p23.x; p4[r][3] = p23.y;
                     q4[r][0] = q01.x; q4[r][1] = q01.y; q4[r][2] = q23.x; q4[r][3] = q23.y;
                 } else {
@@ -319,11 +330,12 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
                     lam[r][c] = l;
                     rs[r] += l;
                     cs[c] += l;
+                    dd[r] = fma(l - lt, l - lt, dd[r]);  // ||lambda^k - lambda~^k||^2 (adaptive step)
                 }
                 if (rv[r] && cv) {
                     const long long off = (long long)ir[r] * a.ld + jl;
-                    st_stream2(a.Q + off, make_double2(lam[r][0], lam[r][1]));
-                    st_stream2(a.Q + off + 2, make_double2(lam[r][2], lam[r][3]));
+                    st_stream2(Rp + off, make_double2(lam[r][0], lam[r][1]));
+                    st_stream2(Rp + off + 2, make_double2(lam[r][2], lam[r][3]));
                 }
             }
             double *cw = cred + ((chunk & 1) * WARPS + warp) * kChunk + 4 * lane;
@@ -366,6 +378,10 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
             }
             const double v = warp_sum(rs[r]);
             if (lane == 0 && rv[r]) dst[NP] = v;
+            if (a.adaptive) {
+                const double dv = warp_sum(dd[r]);
+                if (lane == 0 && rv[r]) a.dpart[(long long)sp * a.N + ir[r]] = dv;
+            }
         }
     }
 }

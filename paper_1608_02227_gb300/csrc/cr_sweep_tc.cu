@@ -260,10 +260,10 @@ __device__ __forceinline__ Item item_of(const TcSweepArgs &a, int item) {
 // lambda = max(0, lambda~ + s rho), rho = (u_h - y_h) + (u_l - y_l) + S; the new lambda
 // overwrites P and its TF32 low part overwrites Q (both 128-byte swizzled).  EDGE adds the
 // zeroing of the diagonal and of padding rows and columns.
-template <bool EDGE>
+template <bool EDGE, bool ADAPT>
 __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, const float (&v)[kC], int r,
                                           float2 uh2, float2 ul2, float2 beta2, float2 s2, bool rv, int i,
-                                          long long j0, int N) {
+                                          long long j0, int N, float &dsum) {
     const float2 m1 = make_float2(-1.f, -1.f);
     const int rx = r & 7;
 #pragma unroll
@@ -277,7 +277,7 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
         const float2 qv[2] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w)};
         const float2 yhv[2] = {make_float2(yh.x, yh.y), make_float2(yh.z, yh.w)};
         const float2 ylv[2] = {make_float2(yl.x, yl.y), make_float2(yl.z, yl.w)};
-        float l[4], lo[4];
+        float l[4], lo[4], sr[4], ltv[4];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const float2 sv = make_float2(v[4 * g + 2 * e], v[4 * g + 2 * e + 1]);
@@ -286,6 +286,11 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
             const float2 w = __ffma2_rn(s2, rho, lt);
             l[2 * e] = fmaxf(0.f, w.x);
             l[2 * e + 1] = fmaxf(0.f, w.y);
+            if (ADAPT) {
+                const float2 srv = __fmul2_rn(s2, rho);
+                sr[2 * e] = srv.x, sr[2 * e + 1] = srv.y;
+                ltv[2 * e] = lt.x, ltv[2 * e + 1] = lt.y;
+            }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -294,6 +299,10 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
                 if (!rv || j >= N || j == i) l[e] = 0.f;
             }
             lo[e] = tf32_lo(l[e]);
+            if (ADAPT) {  // lambda^k - lambda~^k without cancellation: s rho where the step is not clipped
+                const float d = l[e] > 0.f ? sr[e] : -ltv[e];
+                dsum = fmaf(d, d, dsum);
+            }
         }
         *reinterpret_cast<float4 *>(P + off) = make_float4(l[0], l[1], l[2], l[3]);
         *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
@@ -301,9 +310,7 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    sweep_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
-                    const __grid_constant__ CUtensorMap tmQs,
-                    const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
+    sweep_tc_kernel(const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
                     const __grid_constant__ CUtensorMap tmXT, const __grid_constant__ CUtensorMap tmY,
                     const TcSweepArgs a) {
     extern __shared__ unsigned char smem_raw[];
@@ -332,6 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int items = a.row_blocks * a.col_splits;
+    // buffer roles: lambda^{k-1} and lambda^{k-2} are loaded, the output is stored by warps
+    int bp, bq, br;
+    lam_roles(a.st, a.adaptive, a.p_host, &bp, &bq, &br);
+    const CUtensorMap *tmP = a.lmaps + bp, *tmQ = a.lmaps + bq, *tmQs = a.smaps + br;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -388,8 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     unsigned char *st = stage0 + (size_t)s * kStageBytes;
                     bar_expect(&full[s], kTxStage);
-                    tma_load(st + kOffP, &tmP, &full[s], j0, it.i0);
-                    tma_load(st + kOffQ, &tmQ, &full[s], j0, it.i0);
+                    tma_load(st + kOffP, tmP, &full[s], j0, it.i0);
+                    tma_load(st + kOffQ, tmQ, &full[s], j0, it.i0);
                     tma_load(st + kOffXT, &tmXT, &full[s], j0, 0);
                     tma_load(y0 + (size_t)s * kYBytes, &tmY, &full[s], j0, 0);
                 }
@@ -552,6 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (h == 0 && item + (int)gridDim.x < items) ok = put_xi(item + gridDim.x, itn + 1) && ok;
             const float uh = a.u[i], ul = a.u[a.ldv + i];  // i < ldv
             const float2 uh2 = make_float2(uh, uh), ul2 = make_float2(ul, ul);
+            float dsum = 0.f;  // this thread's part of the row's ||lambda^k - lambda~^k||^2
             for (int c = 0; c < it.nch; ++c, ++fill) {
                 if (c > 0 && (c & 1) == 0) ++pair;
                 if ((c & 1) != h) continue;  // the other group's chunk
@@ -574,16 +586,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float *Qs = reinterpret_cast<float *>(st + kOffQ);
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > a.N) ||
                                       (it.i0 + kM > a.N);
-                    if (edge)
-                        epi_chunk<true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N);
-                    else
-                        epi_chunk<false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N);
+                    if (a.adaptive) {
+                        if (edge)
+                            epi_chunk<true, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                        else
+                            epi_chunk<false, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                    } else if (edge) {
+                        epi_chunk<true, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                    } else {
+                        epi_chunk<false, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                    }
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
                 }
                 __syncwarp();
                 if (lane == 0) {
                     // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
-                    if (ok && it.i0 + 32 * q < a.N) tma_store(&tmQs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
+                    if (ok && it.i0 + 32 * q < a.N) tma_store(tmQs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
                     bar_arrive(&lamr[s]);
                 }
                 if (ok) {
@@ -650,6 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&aempty[ab]);
+            if (a.adaptive && ok && rv) a.dpart[((long long)it.sp * 2 + h) * a.N + i] = dsum;
             if (ok2 && rv) {
                 float *dst = a.rowpart + ((long long)it.sp * a.N + i) * (a.NP + 1);
 #pragma unroll
@@ -689,7 +708,7 @@ cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cud
     int occ = 0;
     cudaError_t e = sweep_tc_occupancy(&occ);
     if (e != cudaSuccess) return e;
-    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(*m.P, *m.Q, *m.Qs, m.XRh, m.XRl, m.XT, m.Y, a);
+    sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(m.XRh, m.XRl, m.XT, m.Y, a);
     return cudaGetLastError();
 }
 

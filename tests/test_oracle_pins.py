@@ -260,3 +260,61 @@ def test_dual_obj_identities():
         dy = rng.standard_normal(N) * 1e-3
         dx = rng.standard_normal((N, n)) * 1e-3
         assert lag(d["y"] + dy, d["xi"] + dx) >= base - 1e-15
+
+
+# ---------------------------------------------------------------- adaptive step (Section 4)
+def test_adaptive_check_is_the_quadratic_identity():
+    """g_gamma is a concave quadratic in theta, so the left side of Eq. (adaptive-check) minus
+    g(theta~) minus the linear term is exactly -1/2 (||da||^2 + ||db||^2 / gamma) with
+    (da, db) = C^T (theta - theta~); the GPU evaluates the check in that form."""
+    rng = np.random.default_rng(7)
+    inst = cr_synth.make_instance(9, 3, "maxaff", 0.1, 2)
+    gamma = 1e-2
+    for _ in range(3):
+        tt = rng.random((9, 9)) * 0.3
+        th = np.maximum(0.0, tt + rng.normal(0, 0.2, (9, 9)))
+        np.fill_diagonal(tt, 0.0)
+        np.fill_diagonal(th, 0.0)
+        g = oracle.dual_obj(inst.X, inst.ybar, gamma, th)["g"]
+        dt = oracle.dual_obj(inst.X, inst.ybar, gamma, tt)
+        ceta = oracle.c_apply(inst.X, dt["y"], dt["xi"])        # grad g(theta~) = -C eta(theta~)
+        lin = float(np.sum(-ceta * (th - tt)))
+        da, db = oracle.ct_apply(inst.X, th - tt)
+        quad = -0.5 * (float(da @ da) + float(np.sum(db * db)) / gamma)
+        assert abs((g - dt["g"] - lin) - quad) <= 1e-10 * max(1.0, abs(quad))
+
+
+def test_adaptive_oracle_follows_the_step_rule_and_reaches_the_optimum():
+    """s_k = s_{k-1} upsilon^(l_k - 1) with s_0 = L (so log_upsilon(s_K / L) = sum (l_k - 1)),
+    and the iterates reach the exact dense-QP solution like the constant step."""
+    inst = cr_synth.make_instance(7, 2, "sqnorm", 0.1, 4)
+    gamma = 1e-2
+    L = oracle.lipschitz(inst.X, gamma)
+    o = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0)
+    o.step(3000, log=False)
+    tr = np.array(o.trials)
+    assert tr.min() >= 1
+    expo = np.log(o.s[0] / L) / np.log(2.0)
+    assert abs(expo - float(np.sum(tr - 2))) <= 1e-9
+    ref = qp_dense.solve_nnls(inst.X, inst.ybar, gamma)
+    y, xi = o.primal()
+    assert np.linalg.norm(y - ref["y"]) <= 1e-6 * np.linalg.norm(ref["y"])
+    d = o.dual()
+    assert abs(d["g"] - ref["p"]) <= 1e-8 * abs(ref["p"])
+    # the adaptive steps are longer than 1/L on this instance
+    assert o.s[0] < L
+
+
+def test_adaptive_step_needs_fewer_iterations():
+    inst = cr_synth.make_instance(60, 2, "sqnorm", 0.1, 5)
+    gamma = 1e-3
+    L = oracle.lipschitz(inst.X, gamma)
+    res = {}
+    for ad in (False, True):
+        o = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=ad)
+        o.step(400, log=False)
+        d = o.dual()
+        res[ad] = (d["g"], abs(d["r"] - d["g"]) / d["r"])
+    # the dual objective rises faster (both increase towards p*) and the gap is smaller
+    assert res[True][0] > res[False][0]
+    assert res[True][1] < res[False][1]
