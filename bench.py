@@ -217,6 +217,49 @@ def run_batch(args):
     return 0
 
 
+def run_solve(args):
+    """Time to a relative gap `tol` on one instance of the workload: the adaptive step size of
+    Section 4 with and without momentum restart against the constant step 1/L (each capped at
+    --max-sweeps sweeps), mixed precision by default; `value` is the adaptive run with restart.  Reports the solve time through the public API (creation included and
+    separately), sweeps, accepted iterations and the final certificate."""
+    import torch
+
+    import paper_1608_02227_gb300 as crgb
+
+    torch.cuda.set_device(0)
+    prec = {"fp32": crgb.CR_FP32, "fp64": crgb.CR_FP64, "tf32": crgb.CR_MIXED_TF32}[args.precision]
+    spec = dict(cr_synth.WORKLOADS[args.workload])
+    if args.N:
+        spec["N"] = args.N
+    inst = cr_synth.make_instance(**spec)
+    runs = {}
+    for name, rule, restart in (("adaptive_restart", crgb.CR_STEP_ADAPTIVE, 1), ("adaptive", crgb.CR_STEP_ADAPTIVE, 0),
+                                ("constant", crgb.CR_STEP_CONSTANT, 0)):
+        if rule == crgb.CR_STEP_ADAPTIVE and prec == crgb.CR_FP32:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, step_rule=rule, restart=restart,
+                         check_every=args.check_every) as s:
+            t1 = time.perf_counter()
+            ok, g = s.solve(args.tol, args.max_sweeps)
+            t2 = time.perf_counter()
+        runs[name] = {"converged": bool(ok), "solve_s": t2 - t1, "create_s": t1 - t0, "sweeps": g["sweeps"],
+                      "iterations": g["k"], "rel_gap": g["rel_gap"], "dual_g": g["dual_g"],
+                      "cert_gap_rel": g["cert_gap_rel"], "ms_per_sweep": 1e3 * (t2 - t1) / max(1, g["sweeps"])}
+    best = runs.get("adaptive_restart", runs["constant"])
+    line = {"metric": "solves_per_s", "value": 1.0 / (best["solve_s"] + best["create_s"]), "unit": "solves/s",
+            "n_gpus": 1, "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != crgb.CR_FP64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": inst.N, "n": inst.n, "gamma": GAMMA, "tol": args.tol,
+                       "precision": args.precision, "check_every": args.check_every,
+                       "max_sweeps": args.max_sweeps},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Poisson stream (rate args.rate) of `count` requests: N log-uniform in [200, N_max], n in
     {2..32}, f0 drawn from {||x||^2, max of 10 affine, log-sum-exp of 8}, noise 0.1; each to
@@ -287,9 +330,12 @@ def main():
                     help="tf32: FP32 multipliers with hi+lo TF32 tensor-core contractions (the mixed-precision "
                          "configuration of the N = 20000 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "batch", "serve"],
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "batch", "serve", "solve"],
                     help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances; "
-                         "serve: Poisson request stream through the serving runtime")
+                         "serve: Poisson request stream through the serving runtime; solve: time to the "
+                         "gap on one instance, adaptive vs constant step")
+    ap.add_argument("--max-sweeps", type=int, default=40000, help="sweep cap of each run in --mode solve")
+    ap.add_argument("--check-every", type=int, default=100, help="sweeps between gap checks in --mode solve")
     ap.add_argument("--rate", type=float, default=20.0, help="requests/s in --mode serve")
     ap.add_argument("--N-max", type=int, default=4000, help="largest N of a request in --mode serve")
     ap.add_argument("--count", type=int, default=256, help="instances in --mode batch")
@@ -301,6 +347,8 @@ def main():
         return run_reference(args)
     if args.mode == "batch":
         return run_batch(args)
+    if args.mode == "solve":
+        return run_solve(args)
     if args.mode == "serve":
         return run_serve(args)
 

@@ -88,6 +88,8 @@ typedef struct cr_options {
     int deterministic;   /* kept for ABI stability: every reduction is already in a fixed order */
     int step_rule;       /* cr_step_rule: CR_STEP_CONSTANT (1/L, Figure "papg") or CR_STEP_ADAPTIVE */
     double upsilon;      /* CR_STEP_ADAPTIVE: the factor upsilon > 1 of the step rule (default 2) */
+    int restart;         /* 1: reset the momentum (t = 1) when g_gamma(lambda^k) < g_gamma(lambda^{k-1}),
+                            function-value restart of the accelerated iteration (not in the paper) */
 } cr_options;
 
 /* Convergence record for eta(lambda^k), the primal of Theorem "rate". */

@@ -58,7 +58,7 @@ def _load():
             lib.cro_dual_obj.restype = d
             lib.cro_papg.argtypes = [i, i, _dp, _dp, d, d, i, i, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.cro_papg.restype = i
-            lib.cro_papg_adaptive.argtypes = [i, i, _dp, _dp, d, d, d, i, i, _dp, _dp, _dp, _dp, _ip, _dp]
+            lib.cro_papg_adaptive.argtypes = [i, i, _dp, _dp, d, d, d, i, i, i, _dp, _dp, _dp, _dp, _dp, _ip, _dp]
             lib.cro_papg_adaptive.restype = i
             lib.cro_certify.argtypes = [i, i, _dp, _dp, d, _dp, _dp, _dp, _ip, _dp]
             lib.cro_threads.restype = i
@@ -138,8 +138,10 @@ class PAPG:
     ``adaptive=True`` Step 2 uses the adaptive step size of Section 4 (Eq. (adaptive-check),
     s_k = s_{k-1} upsilon^(l_k - 1), s_0 = L); the log then holds g and the trial counts."""
 
-    def __init__(self, X, ybar, gamma, L, accel=True, theta0=None, adaptive=False, upsilon=2.0):
+    def __init__(self, X, ybar, gamma, L, accel=True, theta0=None, adaptive=False, upsilon=2.0, restart=False):
         self.adaptive = bool(adaptive)
+        self.restart = bool(restart)
+        self.g_prev = np.array([np.nan])
         self.upsilon = float(upsilon)
         self.s = np.array([float(L)])    # s_0 = L (adaptive step rule)
         self.trials = []
@@ -161,8 +163,9 @@ class PAPG:
             tr = np.empty(iters, dtype=np.int32)
             lg_ = np.empty(iters) if log else None
             rc = _load().cro_papg_adaptive(N, n, _p(self.X), _p(self.ybar), self.gamma, self.L, self.upsilon,
-                                           int(iters), int(self.accel), _p(self.theta), _p(self.theta_tilde),
-                                           _p(self.t), _p(self.s), tr.ctypes.data_as(_ip), _p(lg_))
+                                           int(iters), int(self.accel), int(self.restart), _p(self.theta),
+                                           _p(self.theta_tilde), _p(self.t), _p(self.s), _p(self.g_prev),
+                                           tr.ctypes.data_as(_ip), _p(lg_))
             if rc == -1:
                 raise MemoryError("oracle iteration could not allocate its work arrays")
             if rc == -2:

@@ -216,14 +216,15 @@ int cro_papg(int N, int n, const double *X, const double *ybar, double gamma, do
  * which is how it is evaluated here (C^T applied to D over all pairs): the literal form
  * subtracts nearly equal objective values once the steps are small.  A test pins the
  * identity against the literal form.
- * In/out: th_prev, th_tilde, *t as in cro_papg; *s: s_{k-1} -> s_{k-1+iters}.
+ * In/out: th_prev, th_tilde, *t as in cro_papg; *s: s_{k-1} -> s_{k-1+iters}; *g_prev:
+ * g(theta^{k-1}) for the restart test (NaN before the first iteration).
  * trials (length iters, may be NULL): l_k + 1, the candidate steps of each iteration.
  * log_g (may be NULL): g(theta^k).  Returns 0, -1 on allocation failure, -2 when no step
  * passes within 200 trials (non-finite data).
  */
 int cro_papg_adaptive(int N, int n, const double *X, const double *ybar, double gamma,
-                      double L, double upsilon, int iters, int accel, double *th_prev,
-                      double *th_tilde, double *t, double *s, int *trials, double *log_g)
+                      double L, double upsilon, int iters, int accel, int restart, double *th_prev,
+                      double *th_tilde, double *t, double *s, double *g_prev, int *trials, double *log_g)
 {
     size_t NN = (size_t)N * N;
     double *y = (double *)malloc((size_t)N * sizeof(double));
@@ -279,16 +280,23 @@ int cro_papg_adaptive(int N, int n, const double *X, const double *ybar, double 
         if (rc) break;
         if (trials) trials[it] = l + 1;
         *s = sk;
-        /* Steps 3 and 4 */
+        /* Steps 3 and 4; with `restart`, t is reset to 1 (no momentum) when
+         * g(theta^k) < g(theta^{k-1}) (function-value restart, not in the paper) */
+        int reset = 0;
+        if (restart) {
+            const double g = cro_dual_obj(N, n, X, ybar, gamma, th_new, ceta, NULL, NULL, NULL, NULL);
+            reset = *g_prev == *g_prev && g < *g_prev;  /* g_prev is NaN before the first iteration */
+            *g_prev = g;
+        }
         const double tk = *t;
         const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-        const double beta = accel ? (tk - 1.0) / tn : 0.0;
+        const double beta = (accel && !reset) ? (tk - 1.0) / tn : 0.0;
 #pragma omp parallel for schedule(static)
         for (long long q = 0; q < (long long)NN; ++q) {
             th_tilde[q] = th_new[q] + beta * (th_new[q] - th_prev[q]);
             th_prev[q] = th_new[q];
         }
-        *t = tn;
+        *t = reset ? 1.0 : tn;
         if (log_g) log_g[it] = cro_dual_obj(N, n, X, ybar, gamma, th_prev, ceta, NULL, NULL, NULL, NULL);
     }
     free(y); free(xi); free(ceta); free(th_new); free(dif); free(da); free(db);

@@ -32,6 +32,7 @@ class cr_options(ctypes.Structure):
         ("deterministic", ctypes.c_int),
         ("step_rule", ctypes.c_int),
         ("upsilon", ctypes.c_double),
+        ("restart", ctypes.c_int),
     ]
 
 

@@ -447,6 +447,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         h.ring = 0;
         h.upsilon = c->opt.upsilon;
         h.inv_L = 1.0 / c->L;
+        h.restart = c->opt.restart ? 1 : 0;
         h.s = c->opt.upsilon / c->L;
     }
     CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));

@@ -360,9 +360,12 @@ __device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int 
             lp[2] = lg;
             const double tk = st->t;
             const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+            const bool reset = st->restart && k > 1 && g < st->prev_g;  // the ascent went backwards
+            st->prev_g = g;
             st->k = k;
-            st->t = tn;
-            st->beta = st->accelerate ? (tk - 1.0) / tn : 0.0;
+            st->t = reset ? 1.0 : tn;
+            st->beta = (st->accelerate && !reset) ? (tk - 1.0) / tn : 0.0;
+            st->restarts += reset ? 1 : 0;
             st->ring = st->ring == 0 ? 2 : st->ring - 1;  // the candidate becomes lambda^k
             st->s = st->s * st->upsilon;
             st->accepted = 1;

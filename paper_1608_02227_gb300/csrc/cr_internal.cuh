@@ -46,6 +46,9 @@ struct DevState {
     int accepted;       // the last candidate passed the check
     double upsilon;     // step factor
     double inv_L;       // 1/L: the step never drops below it, and a candidate at 1/L is always kept
+    int restart;        // momentum reset when the dual objective decreases
+    long long restarts; // resets so far
+    double prev_g;      // g_gamma of the last accepted iterate
     long long sweeps;   // candidate steps taken
     double check_lhs, check_rhs;  // last check: (||da||^2 + ||db||^2/gamma)/s_k <= ||lambda^k - lambda~^k||^2
 };

@@ -1,5 +1,5 @@
-"""Adaptive step size (Section 4, Eq. (adaptive-check)) on the GPU against the FP64 oracle's
-adaptive iteration.
+"""Adaptive step size (Section 4, Eq. (adaptive-check)), with and without function-value
+restart of the momentum, on the GPU against the FP64 oracle's adaptive iteration.
 
 FP64 mode: the accept/reject decisions (candidate steps per iteration) are identical and the
 iterates agree to 1e-10 relative.  CR_MIXED_TF32: the solve reaches the relative gap with far
@@ -44,18 +44,19 @@ def _gpu_trials(s, iters, max_sweeps=1000):
 # iteration (measured: 1e-12 at k = 30, 1e-3 at k = 59 on the first case).  Decision-for-
 # decision and 1e-10 agreement is checked over the first 30 iterations; beyond that the
 # comparison is in outcome (the TF32 solve below).
-@pytest.mark.parametrize("N,n,fam,gamma,seed", [(200, 2, "sqnorm", 1e-3, 0), (150, 5, "maxaff", 1e-4, 1)])
-def test_fp64_adaptive_matches_oracle_decision_for_decision(N, n, fam, gamma, seed):
+@pytest.mark.parametrize("N,n,fam,gamma,seed,restart", [(200, 2, "sqnorm", 1e-3, 0, 0), (150, 5, "maxaff", 1e-4, 1, 0),
+                                                          (200, 10, "lse", 1e-4, 2, 1)])
+def test_fp64_adaptive_matches_oracle_decision_for_decision(N, n, fam, gamma, seed, restart):
     inst = cr_synth.make_instance(N, n, fam, 0.1, seed)
     L = oracle.lipschitz(inst.X, gamma)
     with crgb.Solver(inst.X, inst.ybar, gamma=gamma, lipschitz=L, precision=crgb.CR_FP64,
-                     step_rule=crgb.CR_STEP_ADAPTIVE, upsilon=2.0, graph_iters=0) as s:
+                     step_rule=crgb.CR_STEP_ADAPTIVE, upsilon=2.0, restart=restart, graph_iters=0) as s:
         trials, k = _gpu_trials(s, 30)
         assert k == 30
         y, xi = s.primal()
         lam = s.lam()
         g = s.gap()
-    ref = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0)
+    ref = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0, restart=bool(restart))
     ref.step(k, log=False)
     assert trials == ref.trials
     y_r, xi_r = ref.primal()
@@ -81,8 +82,9 @@ def test_fp64_adaptive_graph_replay_equals_single_steps():
 
 
 def _oracle_optimum(inst, gamma, L, tol):
-    """The oracle's adaptive iteration run to rel gap <= tol (checked every 100 iterations)."""
-    o = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0)
+    """The oracle's adaptive iteration with restart run to rel gap <= tol (checked every 100
+    iterations, at most 40000)."""
+    o = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0, restart=True)
     rms = float(np.sqrt(np.mean(inst.ybar ** 2)))
     N = inst.N
     for _ in range(400):
@@ -104,7 +106,7 @@ def test_tf32_adaptive_solve_needs_fewer_sweeps_and_finds_the_optimum(N, n, fam,
     res = {}
     for rule in (crgb.CR_STEP_CONSTANT, crgb.CR_STEP_ADAPTIVE):
         with crgb.Solver(inst.X, inst.ybar, gamma=gamma, lipschitz=L, precision=crgb.CR_MIXED_TF32,
-                         step_rule=rule, check_every=50) as s:
+                         step_rule=rule, restart=int(rule == crgb.CR_STEP_ADAPTIVE), check_every=50) as s:
             ok, g = s.solve(tol, cap)
             y, _ = s.primal()
             res[rule] = (ok, g, y)

@@ -318,3 +318,17 @@ def test_adaptive_step_needs_fewer_iterations():
     # the dual objective rises faster (both increase towards p*) and the gap is smaller
     assert res[True][0] > res[False][0]
     assert res[True][1] < res[False][1]
+
+
+def test_adaptive_with_restart_reaches_the_optimum():
+    """Function-value restart (t reset when g decreases) keeps the fixed point: the iterates
+    reach the exact dense-QP solution."""
+    inst = cr_synth.make_instance(8, 2, "maxaff", 0.1, 6)
+    gamma = 1e-2
+    L = oracle.lipschitz(inst.X, gamma)
+    o = oracle.PAPG(inst.X, inst.ybar, gamma, L, adaptive=True, upsilon=2.0, restart=True)
+    o.step(3000, log=False)
+    ref = qp_dense.solve_nnls(inst.X, inst.ybar, gamma)
+    y, _ = o.primal()
+    assert np.linalg.norm(y - ref["y"]) <= 1e-6 * np.linalg.norm(ref["y"])
+    assert abs(o.dual()["g"] - ref["p"]) <= 1e-8 * abs(ref["p"])
