@@ -72,8 +72,8 @@ typedef enum {
  *     tries s_k = s_{k-1} upsilon^(l-1) for l = 0, 1, ... and keeps the first step 1/s_k that
  *     satisfies Eq. (adaptive-check); s_0 = L.  Every candidate is one sweep over all pairs; the
  *     decision is taken on the device (three multiplier buffers instead of two), so cr_dual_step
- *     counts candidates (sweeps) and cr_gap_info.k counts accepted iterations.  Supported with
- *     CR_FP64 and CR_MIXED_TF32 (single instances). */
+ *     counts candidates (sweeps) and cr_gap_info.k counts accepted iterations.  All precisions,
+ *     single instances, batches and the server. */
 typedef enum cr_step_rule { CR_STEP_CONSTANT = 0, CR_STEP_ADAPTIVE = 1 } cr_step_rule;
 
 typedef struct cr_options {
@@ -219,7 +219,8 @@ CR_API cr_status cr_batch_primal(cr_batch *b, int id, double *y, double *xi);
 /* Releases the device memory of instance id (active or retired); the id stays invalid. */
 CR_API cr_status cr_batch_remove(cr_batch *b, int id);
 
-/* Device bytes that an instance of N points in n dimensions takes in a batch. */
+/* Device bytes that an instance of N points in n dimensions takes in a batch with the constant
+ * step (the adaptive step adds a third multiplier buffer, 4 N ceil32(N) bytes, and O(N n)). */
 CR_API long long cr_batch_instance_bytes(long long N, int n);
 
 /* Times `iters` iterations of the active instances for each column-split width in

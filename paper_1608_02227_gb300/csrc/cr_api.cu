@@ -120,6 +120,10 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.rowpart = (float *)c->rowpart;
         a.colpart = (float *)c->colpart;
         a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
+        a.adaptive = c->adaptive ? 1 : 0;
+        a.lmaps = c->tm_ld;
+        for (int i = 0; i < 3; ++i) a.B[i] = (float *)c->lam[i];
+        a.dpart = (float *)c->dpart;
         TmaMaps m = c->tm;
         m.P = &c->tm_lam[P];
         m.Q = &c->tm_lam[Q];
@@ -277,6 +281,10 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         return CR_EUNSUPPORTED;
     }
     choose_split(c);
+    if (c->adaptive && !f64 && !c->tc && !c->tma) {
+        set_err("the adaptive step needs the TMA, tensor-core or FP64 sweep (CR_SWEEP=simple has none)");
+        return CR_EUNSUPPORTED;
+    }
 
     CR_TRY(dev_alloc(c, &c->X, (size_t)N * n));
     CR_TRY(dev_alloc(c, &c->ybar, (size_t)N));
@@ -399,8 +407,13 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_CUDA(make_tmap_2d(&c->tcm.Y, c->yh, c->ldv, 2, c->ldv, 32, 2));
     }
     if (c->tma) {
-        for (int i = 0; i < 2; ++i)
+        memset(c->tm_lam, 0, sizeof(c->tm_lam));
+        for (int i = 0; i < nbuf; ++i)
             CR_CUDA(make_tmap_2d(&c->tm_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, kChunk, c->rows));
+        if (c->adaptive) {
+            CR_TRY(dev_alloc(c, &c->tm_ld, 3));
+            CR_CUDA(cudaMemcpyAsync(c->tm_ld, c->tm_lam, sizeof(c->tm_lam), cudaMemcpyHostToDevice, c->stream));
+        }
         CR_CUDA(make_tmap_2d(&c->tm.X, c->xT32, c->ldv, c->NP, c->ldv, kChunk, c->NP));
         CR_CUDA(make_tmap_2d(&c->tm.Y, c->yh, c->ldv, 2, c->ldv, kChunk, 2));
         CR_CUDA(make_tmap_2d(&c->tm.Xi, c->xiT, c->ldv, c->NP, c->ldv, c->rows, c->NP));
@@ -509,6 +522,11 @@ cr_status gap_launch(cr_ctx *c) {
     long long kk = 0;
     int lb = 0;
     CR_TRY(current_k(c, &kk, &lb));
+    return gap_launch_k(c, kk);
+}
+
+// The same for a known accepted iteration count k (no device round trip).
+cr_status gap_launch_k(cr_ctx *c, long long kk) {
     CertArgs a{};
     a.N = c->N;
     a.n = c->n;
@@ -642,10 +660,7 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
             set_err("upsilon must be finite and > 1");
             return CR_EINVAL;
         }
-        if (o.precision == CR_FP32) {
-            set_err("the adaptive step runs with CR_FP64 or CR_MIXED_TF32");
-            return CR_EUNSUPPORTED;
-        }
+
     }
     if (o.check_every < 1) o.check_every = 1;
     if (o.graph_iters < 0 || (o.graph_iters & 1)) {

@@ -93,8 +93,12 @@ void drop_graph(cr_batch *b) {
 
 void fill_desc(const cr_batch *b, const cr_ctx *c, InstDesc *d, int id) {
     memset(d, 0, sizeof(*d));
-    d->tm_lam[0] = c->tm_lam[0];
-    d->tm_lam[1] = c->tm_lam[1];
+    for (int i = 0; i < 3; ++i) d->tm_lam[i] = c->tm_lam[i];
+    d->lam[2] = (float *)c->lam[2];
+    d->adaptive = c->adaptive ? 1 : 0;
+    d->dpart = (float *)c->dpart;
+    d->ha_c = c->ha_c;
+    d->hb_c = c->hb_c;
     d->tm_x = c->tm.X;
     d->tm_y = c->tm.Y;
     d->tm_xi = c->tm.Xi;
@@ -202,11 +206,13 @@ cr_status enqueue_batch_iteration(cr_batch *b) {
     for (size_t i = 0; i < b->buckets.size(); ++i) {
         const Bucket &bk = b->buckets[i];
         CR_CUDA(cudaStreamWaitEvent(b->aux[i], b->ev_fork, 0));
-        CR_CUDA(launch_sweep_tma_batch(bk.np, b->d_desc, b->d_items + bk.off, bk.count, b->d_err, bk.grid, b->aux[i]));
+        CR_CUDA(launch_sweep_tma_batch(bk.np, b->d_desc, b->d_items + bk.off, bk.count, b->d_err, bk.grid,
+                                       b->opt.step_rule == CR_STEP_ADAPTIVE, b->aux[i]));
         CR_CUDA(cudaEventRecord(b->ev_join[i], b->aux[i]));
         CR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
     }
     CR_CUDA(launch_finalize_batch(b->d_desc, b->d_fin, b->nfin, b->stream));
+    if (b->opt.step_rule == CR_STEP_ADAPTIVE) CR_CUDA(launch_commit_batch(b->d_desc, b->d_fin, b->nfin, b->stream));
     return CR_OK;
 }
 
@@ -257,9 +263,15 @@ cr_status check(cr_batch *b) {
     const int na = (int)b->active.size();
     if (!na) return CR_OK;
     std::vector<DevState> hs(na);
+    if (b->opt.step_rule == CR_STEP_ADAPTIVE) {  // accepted counts live on the device: one round trip
+        for (int di = 0; di < na; ++di)
+            CR_CUDA(cudaMemcpyAsync(&hs[di], b->inst[b->active[di]].c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                    b->stream));
+        CR_CUDA(cudaStreamSynchronize(b->stream));
+    }
     for (int di = 0; di < na; ++di) {
         cr_ctx *c = b->inst[b->active[di]].c;
-        CR_TRY(gap_launch(c));
+        CR_TRY(gap_launch_k(c, b->opt.step_rule == CR_STEP_ADAPTIVE ? hs[di].k : c->k));
         CR_CUDA(cudaMemcpyAsync(&hs[di], c->st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
     }
     int err = 0;

@@ -387,8 +387,7 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_adapt_kernel(const FinArgs
 // history slot of (a,b)^{k-2} and Step 1 of the next iteration builds eta(lambda~^{k+1}) with
 // C^T lambda~^{k+1} = (1 + beta) C^T lambda^k - beta C^T lambda^{k-1}; after a rejected one
 // nothing changes and the next sweep retries from the same lambda~^k.
-__global__ void commit_kernel(const FinArgs a) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void commit_point(const FinArgs &a, const int l) {
     const DevState *st = a.st;
     if (l >= a.N || !st->accepted) return;
     const long long k = st->k;
@@ -426,6 +425,8 @@ __global__ void commit_kernel(const FinArgs a) {
     }
 }
 
+__global__ void commit_kernel(const FinArgs a) { commit_point(a, blockIdx.x * blockDim.x + threadIdx.x); }
+
 // Batched finalize: one CTA per (instance, 32-point block) of the work-list.
 __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDesc *d, const FinItem *items) {
     const FinItem it = items[blockIdx.x];
@@ -458,7 +459,47 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDes
     a.log = D.log;
     a.st = D.st;
     a.init = 0;
-    finalize_body<float>(a, it.block, D.fin_blocks);
+    if (D.adaptive) {
+        a.adaptive = 1;
+        a.a_new = D.ha_c;
+        a.b_new = D.hb_c;
+        for (int i = 0; i < 2; ++i) {
+            a.hist_a[i] = D.ha[i];
+            a.hist_b[i] = D.hb[i];
+        }
+        a.dpart = D.dpart;
+        a.dgroups = D.col_splits;
+        finalize_adapt_body<float>(a, it.block, D.fin_blocks);
+    } else {
+        finalize_body<float>(a, it.block, D.fin_blocks);
+    }
+}
+
+// Batched commit (adaptive step): one warp per (instance, 32-point block) of the work-list.
+__global__ void commit_batch_kernel(const InstDesc *d, const FinItem *items) {
+    const FinItem it = items[blockIdx.x];
+    const InstDesc &D = d[it.inst];
+    FinArgs a{};
+    a.N = D.N;
+    a.n = D.n;
+    a.precision = CR_FP32;
+    a.ldv = D.ldv;
+    a.X = D.X;
+    a.ybar = D.ybar;
+    a.a_new = D.ha_c;
+    a.b_new = D.hb_c;
+    for (int i = 0; i < 2; ++i) {
+        a.hist_a[i] = D.ha[i];
+        a.hist_b[i] = D.hb[i];
+    }
+    a.yh = D.yh;
+    a.yl = D.yl;
+    a.uh = D.uh;
+    a.ul = D.ul;
+    a.xiT = D.xiT;
+    a.xT32 = D.xT32;
+    a.st = D.st;
+    commit_point(a, it.block * kFX + (int)threadIdx.x);
 }
 
 __global__ void primal_kernel(int N, int n, const double *ybar, const double *av, const double *bv,
@@ -539,6 +580,12 @@ cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s) {
     } else {
         finalize_kernel<float><<<g, kFX * kFY, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    commit_batch_kernel<<<nitems, kFX, 0, s>>>(d, items);
     return cudaGetLastError();
 }
 

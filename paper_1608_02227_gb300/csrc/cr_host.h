@@ -46,7 +46,8 @@ struct cr_ctx {
     // sweep shape
     int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
     bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
-    CUtensorMap tm_lam[2];
+    CUtensorMap tm_lam[3];
+    CUtensorMap *tm_ld = nullptr;  // adaptive step: device copy of tm_lam (roles chosen on the device)
     TmaMaps tm{};
     bool tc = false;             // CR_MIXED_TF32: tensor-core sweep (cr_sweep_tc.cu)
     CUtensorMap *tc_ld = nullptr, *tc_st = nullptr;  // device arrays: load / store maps of the buffers
@@ -97,6 +98,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar);
 cr_status fetch_state(const cr_ctx *c, DevState *h);
 cr_status enqueue_iteration(cr_ctx *c, long long k, cudaEvent_t e0, cudaEvent_t e1);
 cr_status gap_launch(cr_ctx *c);
+cr_status gap_launch_k(cr_ctx *c, long long k);
 cr_status gap_finish(const cr_ctx *c, DevState h, cr_gap_info *out);
 
 }  // namespace crh

@@ -135,6 +135,10 @@ cudaError_t sweep_occupancy_d(int np, int *blocks_per_sm);
 // FP32 sweep with the TMA / mbarrier pipeline (cr_sweep_tma.cu)
 struct TmaSweepArgs {
     float *Q;                // lambda^k is written here (the buffer that held lambda^{k-2})
+    int adaptive;            // adaptive step: roles of the three buffers from the device state
+    const CUtensorMap *lmaps;  // adaptive step: device array of the buffers' load maps
+    float *B[3];             // adaptive step: the three buffers
+    float *dpart;            // adaptive step: [S][N] row sums of (lambda^k - lambda~^k)^2
     long long ld;
     int N;
     int row_blocks, col_splits, cols_per_split;
@@ -191,9 +195,12 @@ struct WorkItem {
     int inst, rb, sp;
 };
 struct InstDesc {
-    CUtensorMap tm_lam[2];               // lam[0], lam[1]: [N][ld], box 128 x R
+    CUtensorMap tm_lam[3];               // lam[0..2]: [N][ld], box 128 x R (the third with the adaptive step)
     CUtensorMap tm_x, tm_y, tm_xi, tm_u; // as in TmaMaps
-    float *lam[2];
+    float *lam[3];
+    int adaptive;
+    float *dpart;                        // adaptive step: [S][N] row sums of (lambda^k - lambda~^k)^2
+    double *ha_c, *hb_c;                 // adaptive step: C^T of the candidate
     long long ld, ldv;
     int N, n, NP, cols_per_split;
     int row_blocks, col_splits, fin_blocks, inst_id;
@@ -206,11 +213,13 @@ struct InstDesc {
     double *finblk, *log;
 };
 cudaError_t launch_sweep_tma_batch(int np, const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
-                                   cudaStream_t s);
+                                   bool adaptive, cudaStream_t s);
 struct FinItem {
     int inst, block;
 };
 cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s);
+// adaptive step: the commit of every instance whose candidate was accepted
+cudaError_t launch_commit_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s);
 
 // ---------------------------------------------------------------- finalize + recovery (S1, S3)
 struct FinArgs {

@@ -231,7 +231,9 @@ CR_API cr_status cr_server_submit(cr_server *s, const double *X, const double *y
         set_err("bad argument to cr_server_submit");
         return CR_EINVAL;
     }
-    const long long bytes = cr_batch_instance_bytes(N, n);
+    long long bytes = cr_batch_instance_bytes(N, n);
+    if (s->opt.step_rule == CR_STEP_ADAPTIVE)  // third multiplier buffer, candidate C^T and row sums
+        bytes += N * ((N + 31) / 32 * 32) * 4 + 8 * N * (n + 1) + 4 * N * ((N + 511) / 512 + 1);
     if (bytes > s->mem_cap) {
         set_err("request needs %lld bytes, above the server's cap of %lld", bytes, s->mem_cap);
         return CR_ENOMEM;

@@ -100,7 +100,8 @@ struct TmaShape {
 // Per-item view of the data a work item needs (tensor maps, pointers, tile bounds).
 struct ItemView {
     const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
-    float *Qp;
+    float *Qp;               // lambda^k is written here
+    float *dpart;            // adaptive step: row sums of (lambda^k - lambda~^k)^2, [S][N]
     long long ld, c0, c1;
     int N, i0, rb, sp;
     float *rowpart, *colpart;
@@ -124,6 +125,14 @@ struct SrcSingle {
         ItemView v;
         v.P = P; v.Q = Q; v.X = X; v.Y = Y; v.Xi = Xi; v.U = U;
         v.Qp = a.Q;
+        v.dpart = a.dpart;
+        if (a.adaptive) {  // buffer roles rotate on the device (three buffers)
+            int bp, bq, br;
+            lam_roles(a.st, 1, 0, &bp, &bq, &br);
+            v.P = a.lmaps + bp;
+            v.Q = a.lmaps + bq;
+            v.Qp = br == 0 ? a.B[0] : (br == 1 ? a.B[1] : a.B[2]);  // no dynamic index into the parameters
+        }
         v.ld = a.ld;
         v.N = a.N;
         v.rb = item / a.col_splits;
@@ -151,12 +160,14 @@ struct SrcBatch {
     __device__ __forceinline__ ItemView view(int item, int rows) const {
         const WorkItem wi = w[item];
         const InstDesc &D = d[wi.inst];
-        const int par = (int)(D.st->k & 1);
+        int bp, bq, br;
+        lam_roles(D.st, D.adaptive, (int)(D.st->k & 1), &bp, &bq, &br);
         ItemView v;
-        v.P = &D.tm_lam[par];
-        v.Q = &D.tm_lam[par ^ 1];
+        v.P = &D.tm_lam[bp];
+        v.Q = &D.tm_lam[bq];
         v.X = &D.tm_x; v.Y = &D.tm_y; v.Xi = &D.tm_xi; v.U = &D.tm_u;
-        v.Qp = D.lam[par ^ 1];
+        v.Qp = D.lam[br];
+        v.dpart = D.dpart;
         v.ld = D.ld;
         v.N = D.N;
         v.rb = wi.rb;
@@ -171,7 +182,7 @@ struct SrcBatch {
     }
 };
 
-template <int NP, class Src>
+template <int NP, bool ADAPT, class Src>
 __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
     using S = TmaShape<NP>;
     constexpr int MR = S::MR, CW = S::CW, STAGES = S::STAGES, XB = S::XB, kRowsT = S::kRowsT;
@@ -259,6 +270,9 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
             float uh[MR], ul[MR];
             float2 Bp[MR / 2][NP];
             float2 rs2[MR / 2];
+            float dd[MR];  // adaptive step: this lane's part of ||lambda^k - lambda~^k||^2 per row
+#pragma unroll
+            for (int r = 0; r < MR; ++r) dd[r] = 0.f;
 #pragma unroll
             for (int p = 0; p < MR / 2; ++p) {
                 rs2[p] = make_float2(0.f, 0.f);
@@ -338,6 +352,14 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                                 const long long j = j0 + 4 * lane + c;
                                 if (i >= NN || j >= NN || j == i) lam[r][c] = 0.f;
                             }
+                        }
+                        if constexpr (ADAPT) {  // s rho where the step is not clipped: no cancellation
+                            const float2 sra = __fmul2_rn(s2, d[r][0]), srb = __fmul2_rn(s2, d[r][1]);
+                            const float e0 = lam[r][0] > 0.f ? sra.x : -lta.x;
+                            const float e1 = lam[r][1] > 0.f ? sra.y : -lta.y;
+                            const float e2 = lam[r][2] > 0.f ? srb.x : -ltb.x;
+                            const float e3 = lam[r][3] > 0.f ? srb.y : -ltb.y;
+                            dd[r] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd[r]))));
                         }
                         if (4 * lane + j0 < c1 && i0 + rloc + r < NN)
                             __stcs(reinterpret_cast<float4 *>(v.Qp + (long long)(i0 + rloc + r) * ld + j0 + 4 * lane),
@@ -432,26 +454,36 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                     if (ib < NN) db[NP] = vy;
                 }
             }
+            if constexpr (ADAPT) {
+#pragma unroll
+                for (int r = 0; r < MR; ++r) {
+                    float v2 = dd[r];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                    const int i = i0 + rloc + r;
+                    if (lane == 0 && i < NN) v.dpart[(long long)sp * NN + i] = v2;
+                }
+            }
         }
     }
 }
 
 
-template <int NP>
+template <int NP, bool ADAPT>
 __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
     sweep_tma_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
                      const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                      const __grid_constant__ CUtensorMap tmXi, const __grid_constant__ CUtensorMap tmU,
                      const TmaSweepArgs a) {
     SrcSingle src{&tmP, &tmQ, &tmX, &tmY, &tmXi, &tmU, a};
-    sweep_body<NP>(src, a.err);
+    sweep_body<NP, ADAPT>(src, a.err);
 }
 
-template <int NP>
+template <int NP, bool ADAPT>
 __global__ void __launch_bounds__(TmaShape<NP>::THREADS, 1)
     sweep_tma_batch_kernel(const InstDesc *d, const WorkItem *w, int nitems, int *err) {
     SrcBatch src{d, w, nitems};
-    sweep_body<NP>(src, err);
+    sweep_body<NP, ADAPT>(src, err);
 }
 
 #define CR_NP_LIST(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32)
@@ -461,10 +493,14 @@ int tma_diag_regs = 0, tma_diag_maxthreads = 0, tma_diag_smem = 0, tma_diag_thre
 template <int NP>
 cudaError_t run_tma(const TmaMaps &m, const TmaSweepArgs &a, int grid, cudaStream_t st, int *occ) {
     using S = TmaShape<NP>;
-    auto k = sweep_tma_kernel<NP>;
+    auto k = a.adaptive ? sweep_tma_kernel<NP, true> : sweep_tma_kernel<NP, false>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<NP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sweep_tma_kernel<NP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)S::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -497,12 +533,17 @@ cudaError_t launch_sweep_tma(int np, const TmaMaps &m, const TmaSweepArgs &a, in
 }
 
 template <int NP>
-cudaError_t run_tma_batch(const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid, cudaStream_t st) {
+cudaError_t run_tma_batch(const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid, bool adaptive,
+                          cudaStream_t st) {
     using S = TmaShape<NP>;
-    auto k = sweep_tma_batch_kernel<NP>;
+    auto k = adaptive ? sweep_tma_batch_kernel<NP, true> : sweep_tma_batch_kernel<NP, false>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(sweep_tma_batch_kernel<NP, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sweep_tma_batch_kernel<NP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)S::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -511,10 +552,10 @@ cudaError_t run_tma_batch(const InstDesc *d, const WorkItem *w, int nitems, int 
 }
 
 cudaError_t launch_sweep_tma_batch(int np, const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
-                                   cudaStream_t s) {
+                                   bool adaptive, cudaStream_t s) {
     switch (np) {
 #define CASE(V) \
-    case V: return run_tma_batch<V>(d, w, nitems, err, grid, s);
+    case V: return run_tma_batch<V>(d, w, nitems, err, grid, adaptive, s);
         CR_NP_LIST(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

@@ -126,9 +126,9 @@ def test_tf32_adaptive_solve_needs_fewer_sweeps_and_finds_the_optimum(N, n, fam,
     assert rel(y_a, y_ref) <= 1e-2
 
 
-def test_adaptive_rejects_unsupported_options():
+def test_adaptive_rejects_bad_options():
     inst = cr_synth.make_instance(50, 2, "sqnorm", 0.1, 6)
     with pytest.raises(crgb.CRError):
-        crgb.Solver(inst.X, inst.ybar, precision=crgb.CR_FP32, step_rule=crgb.CR_STEP_ADAPTIVE)
-    with pytest.raises(crgb.CRError):
         crgb.Solver(inst.X, inst.ybar, precision=crgb.CR_FP64, step_rule=crgb.CR_STEP_ADAPTIVE, upsilon=1.0)
+    with pytest.raises(crgb.CRError):
+        crgb.Solver(inst.X, inst.ybar, precision=crgb.CR_FP32, step_rule=7)
