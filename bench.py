@@ -170,11 +170,18 @@ def cpu_baseline(workload):
             "sample": f"first {Ns} points of {workload}, {iters} FP64 oracle iterations ({dt:.1f} s)"}
 
 
+def _rule_options(crgb, rule):
+    if rule == "adaptive":
+        return dict(step_rule=crgb.CR_STEP_ADAPTIVE, upsilon=2.0, restart=1)
+    return dict(step_rule=crgb.CR_STEP_CONSTANT)
+
+
 def run_batch(args):
     """Batched solves: `count` instances (N log-uniform in [100, 4000], n in {2..16},
     f0 = ||x||^2 + N(0, 0.1^2)), all submitted at t = 0 into one cr_batch, each retired at
     rel_gap <= tol.  Reports solves/s, lambda-pair updates/s and completion-time p50/p99,
-    against the same instances solved one after another with the single-instance path."""
+    against the same instances solved one after another with the single-instance path and the
+    same step rule (within --plain-budget seconds; the rate is over the instances it finished)."""
     import torch
 
     import paper_1608_02227_gb300 as crgb
@@ -183,11 +190,12 @@ def run_batch(args):
     insts = cr_synth.batch_workload(args.count, seed=0)
     check = 100
     max_iter = 200000
+    ropt = _rule_options(crgb, args.rule)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     done_at = {}
     pairs = 0.0
-    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check) as b:
+    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check, **ropt) as b:
         ids = [b.add(i.X, i.ybar, tol=args.tol, max_iter=max_iter) for i in insts]
         t_setup = time.perf_counter() - t0
         width = b.autotune(2)
@@ -201,18 +209,31 @@ def run_batch(args):
         infos = [b.poll(i) for i in ids]
     wall = time.perf_counter() - t0
     for inst, (done, st, info) in zip(insts, infos):
-        pairs += inst.N * (inst.N - 1) * info["k"]
+        pairs += inst.N * (inst.N - 1) * info["sweeps"]
     lat = sorted(done_at.values())
     conv = sum(1 for d, st, _ in infos if st == 0)
+    # the plain single-instance path: one cr_solve after another, same options
+    t1 = time.perf_counter()
+    plain_done, plain_conv = 0, 0
+    for inst in insts:
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20, **ropt) as s:
+            ok, _ = s.solve(args.tol, max_iter)
+        plain_done += 1
+        plain_conv += int(ok)
+        if time.perf_counter() - t1 > args.plain_budget:
+            break
+    plain_wall = time.perf_counter() - t1
     line = {"metric": "solves_per_s", "value": len(insts) / wall, "unit": "solves/s", "n_gpus": 1,
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch{len(insts)}_sqnorm_N100-4000_n2-16", "gamma": GAMMA, "tol": args.tol,
-                       "check_every": check, "tile_cols": width},
+                       "check_every": check, "tile_cols": width, "step_rule": args.rule},
             "converged": conv, "lambda_pairs_per_s": pairs / wall, "setup_s": t_setup, "wall_s": wall,
             "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                           "max": lat[-1]},
-            "iterations": {"min": min(i[2]["k"] for i in infos), "max": max(i[2]["k"] for i in infos)}}
+            "sweeps": {"min": min(i[2]["sweeps"] for i in infos), "max": max(i[2]["sweeps"] for i in infos)},
+            "plain_single_instance": {"solves_per_s": plain_done / plain_wall, "instances": plain_done,
+                                      "converged": plain_conv, "wall_s": plain_wall}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -263,9 +284,9 @@ def run_solve(args):
 def run_serve(args):
     """Poisson stream (rate args.rate) of `count` requests: N log-uniform in [200, N_max], n in
     {2..32}, f0 drawn from {||x||^2, max of 10 affine, log-sum-exp of 8}, noise 0.1; each to
-    rel_gap <= tol (cap 20000 iterations).  Served with continuous batching (60 GB cap), then
+    rel_gap <= tol (cap 20000 sweeps).  Served with continuous batching (60 GB cap), then
     the same stream on the plain single-instance path (one solve at a time, FIFO, same
-    arrival times, cr_solve with the same check interval)."""
+    arrival times, cr_solve with the same check interval and step rule)."""
     import torch
 
     import paper_1608_02227_gb300 as crgb
@@ -275,8 +296,9 @@ def run_serve(args):
     max_iter, check = 20000, 100
     # continuous batching
     t0 = time.perf_counter()
+    ropt = _rule_options(crgb, args.rule)
     with crgb.Server(mem_cap_bytes=60 << 30, max_active=256, gamma=GAMMA, check_every=check,
-                     graph_iters=20) as srv:
+                     graph_iters=20, **ropt) as srv:
         ids = []
         for t_arr, inst in reqs:
             delay = t_arr - (time.perf_counter() - t0)
@@ -298,7 +320,7 @@ def run_serve(args):
     for t_arr, inst in reqs:
         start = max(clock, t_arr)
         s0 = time.perf_counter()
-        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20) as s:
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20, **ropt) as s:
             ok, rec = s.solve(args.tol, max_iter)
         clock = start + (time.perf_counter() - s0)
         lat_plain.append(clock - t_arr)
@@ -311,7 +333,8 @@ def run_serve(args):
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serve_poisson{args.rate:g}_{len(reqs)}req_N200-{args.N_max}_n2-32",
-                       "gamma": GAMMA, "tol": args.tol, "max_iter": max_iter, "mem_cap_GB": 60},
+                       "gamma": GAMMA, "tol": args.tol, "max_iter": max_iter, "mem_cap_GB": 60,
+                       "step_rule": args.rule},
             "served": served, "plain_single_instance": plain,
             "offered_rate": args.rate, "achieved_rate": served["solves_per_s"]}
     print(json.dumps(line), flush=True)
@@ -336,6 +359,11 @@ def main():
                          "gap on one instance, adaptive vs constant step")
     ap.add_argument("--max-sweeps", type=int, default=40000, help="sweep cap of each run in --mode solve")
     ap.add_argument("--check-every", type=int, default=100, help="sweeps between gap checks in --mode solve")
+    ap.add_argument("--rule", default="adaptive", choices=["adaptive", "constant"],
+                    help="step rule of --mode batch / serve: adaptive (Section 4, with momentum restart) or "
+                         "constant 1/L")
+    ap.add_argument("--plain-budget", type=float, default=120.0,
+                    help="seconds for the one-after-another single-instance comparison in --mode batch")
     ap.add_argument("--rate", type=float, default=20.0, help="requests/s in --mode serve")
     ap.add_argument("--N-max", type=int, default=4000, help="largest N of a request in --mode serve")
     ap.add_argument("--count", type=int, default=256, help="instances in --mode batch")

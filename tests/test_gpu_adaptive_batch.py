@@ -65,3 +65,29 @@ def test_batch_adaptive_retires_with_fewer_sweeps():
     sw_a = sum(info["sweeps"] for _, _, info in res["adapt"])
     sw_c = sum(info["sweeps"] for _, _, info in res["const"])
     assert sw_a < sw_c
+
+
+def test_served_adaptive_results_equal_alone():
+    """Under the adaptive step the served result is the instance solved alone for the same
+    number of sweeps (the accept/reject decisions are the instance's own)."""
+    import time
+    rng = np.random.default_rng(4)
+    insts = [cr_synth.make_instance(int(rng.integers(500, 1500)), int(rng.integers(2, 10)),
+                                    ["sqnorm", "maxaff", "lse"][r % 3], 0.1, 2000 + r) for r in range(6)]
+    gamma = 1e-3
+    with crgb.Server(mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25, graph_iters=4,
+                     **ADAPT) as srv:
+        ids = []
+        for inst in insts:
+            ids.append(srv.submit(inst.X, inst.ybar, tol=1e-4, max_iter=3000))
+            time.sleep(0.02)
+        for r in ids:
+            srv.wait(r, 300)
+        res = [(srv.poll(r), srv.result(r)) for r in ids]
+    for inst, ((state, status, info, lat), (y, xi)) in zip(insts, res):
+        assert state == 2 and status in (0, 4)
+        with crgb.Solver(inst.X, inst.ybar, gamma=gamma, tile_cols=512, graph_iters=0, **ADAPT) as s:
+            s.step(int(info["sweeps"]))
+            ys, xis = s.primal()
+            assert s.gap()["k"] == info["k"]
+        assert np.array_equal(y, ys) and np.array_equal(xi, xis), (inst.N, inst.n)
