@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kMaxBuckets = 12;
 constexpr int kMinSplit = 512;  // smallest column-split width (sizes the row partials)
+constexpr int kDefaultSplit = 4096;
 
 struct BatchInst {
     cr_ctx *c = nullptr;
@@ -346,6 +347,9 @@ CR_API cr_status cr_batch_create(const cr_options *opt, void *stream, cr_batch *
         return CR_ENOMEM;
     }
     b->opt = o;
+    // column-split width: the caller's tile_cols, else 4096 (what the autotuner picks for the
+    // 256-instance workload; 512-wide splits cost ~8x the items on large instances)
+    b->cps = o.tile_cols > 0 ? (int)round_up(std::max(o.tile_cols, kMinSplit), kChunk) : kDefaultSplit;
     cudaError_t e = cudaSuccess;
     if (stream) {
         b->stream = (cudaStream_t)stream;

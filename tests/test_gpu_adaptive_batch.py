@@ -42,7 +42,7 @@ def test_batch_adaptive_bitwise_matches_single():
                          **ADAPT) as s:
             s.step(37)
             solo.append(s.primal())
-    with crgb.Batch(gamma=1e-4, graph_iters=0, check_every=1000, **ADAPT) as b:
+    with crgb.Batch(tile_cols=512, gamma=1e-4, graph_iters=0, check_every=1000, **ADAPT) as b:
         ids = [b.add(i.X, i.ybar, tol=0.0, max_iter=10 ** 6) for i in insts]
         b.step(37)
         for i, (y, xi) in zip(ids, solo):
@@ -54,7 +54,7 @@ def test_batch_adaptive_retires_with_fewer_sweeps():
     insts = cr_synth.batch_workload(24, seed=3)
     res = {}
     for name, extra in (("const", {}), ("adapt", ADAPT)):
-        with crgb.Batch(gamma=1e-4, graph_iters=20, check_every=100, **extra) as b:
+        with crgb.Batch(tile_cols=512, gamma=1e-4, graph_iters=20, check_every=100, **extra) as b:
             ids = [b.add(i.X, i.ybar, tol=1e-4, max_iter=60000) for i in insts]
             b.run()
             polls = [b.poll(i) for i in ids]
@@ -75,7 +75,7 @@ def test_served_adaptive_results_equal_alone():
     insts = [cr_synth.make_instance(int(rng.integers(500, 1500)), int(rng.integers(2, 10)),
                                     ["sqnorm", "maxaff", "lse"][r % 3], 0.1, 2000 + r) for r in range(6)]
     gamma = 1e-3
-    with crgb.Server(mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25, graph_iters=4,
+    with crgb.Server(tile_cols=512, mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25, graph_iters=4,
                      **ADAPT) as srv:
         ids = []
         for inst in insts:

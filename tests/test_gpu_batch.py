@@ -28,7 +28,7 @@ def _instances(shapes, seed0=100, family="sqnorm"):
 
 def test_batch_bitwise_matches_single():
     insts = _instances(SHAPES)
-    with crgb.Batch(gamma=1e-4, graph_iters=8) as b:
+    with crgb.Batch(tile_cols=512, gamma=1e-4, graph_iters=8) as b:
         ids = [b.add(i.X, i.ybar, tol=0.0, max_iter=10**9) for i in insts]
         b.step(3)
         b.step(37)
@@ -45,7 +45,7 @@ def test_batch_bitwise_matches_single():
 
 def test_batch_instances_added_midway():
     insts = _instances(SHAPES[:5], seed0=200)
-    with crgb.Batch(gamma=1e-4, graph_iters=4) as b:
+    with crgb.Batch(tile_cols=512, gamma=1e-4, graph_iters=4) as b:
         ids = [b.add(i.X, i.ybar, tol=0.0, max_iter=10**9) for i in insts[:3]]
         b.step(11)
         ids += [b.add(i.X, i.ybar, tol=0.0, max_iter=10**9) for i in insts[3:]]
@@ -63,7 +63,7 @@ def test_batch_retires_each_instance_and_matches_oracle():
     shapes = [(60, 2), (90, 4), (120, 8), (75, 3)]
     insts = _instances(shapes, seed0=300)
     gamma, tol = 1e-2, 1e-4
-    with crgb.Batch(gamma=gamma, graph_iters=8, check_every=50) as b:
+    with crgb.Batch(tile_cols=512, gamma=gamma, graph_iters=8, check_every=50) as b:
         ids = [b.add(i.X, i.ybar, tol=tol, max_iter=200000) for i in insts]
         b.run()
         res = []
@@ -84,7 +84,7 @@ def test_batch_retires_each_instance_and_matches_oracle():
 
 def test_batch_autotune_and_remove():
     insts = _instances(SHAPES[:4], seed0=400)
-    with crgb.Batch(gamma=1e-4, graph_iters=0) as b:
+    with crgb.Batch(tile_cols=512, gamma=1e-4, graph_iters=0) as b:
         ids = [b.add(i.X, i.ybar, tol=0.0, max_iter=10**9) for i in insts]
         w = b.autotune(2)
         assert w in (512, 1024, 2048, 4096, 1 << 30)
@@ -108,7 +108,7 @@ def test_instance_bytes_is_an_upper_bound():
         inst = cr_synth.make_instance(N, n, "sqnorm", 0.1, 1)
         torch.cuda.synchronize()
         free0, _ = torch.cuda.mem_get_info()
-        with crgb.Batch(gamma=1e-4) as b:
+        with crgb.Batch(tile_cols=512, gamma=1e-4) as b:
             b.add(inst.X, inst.ybar)
             torch.cuda.synchronize()
             free1, _ = torch.cuda.mem_get_info()

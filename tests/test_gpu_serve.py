@@ -31,7 +31,7 @@ def test_served_results_equal_alone_and_requests_overlap():
     insts = _stream(8)
     gamma = 1e-3
     max_running = 0
-    with crgb.Server(mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25, graph_iters=4) as srv:
+    with crgb.Server(tile_cols=512, mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25, graph_iters=4) as srv:
         ids = []
         for inst in insts:
             ids.append(srv.submit(inst.X, inst.ybar, tol=1e-4, max_iter=3000))
@@ -55,7 +55,7 @@ def test_admission_respects_the_memory_cap():
     insts = _stream(6, seed=1, N_lo=1500, N_hi=1600, n_lo=4, n_hi=4)
     need = max(crgb.cr_batch_instance_bytes(i.N, i.n) for i in insts)
     cap = 2 * need + need // 2           # room for two instances at a time
-    with crgb.Server(mem_cap_bytes=cap, max_active=64, gamma=1e-3, check_every=20, graph_iters=4) as srv:
+    with crgb.Server(tile_cols=512, mem_cap_bytes=cap, max_active=64, gamma=1e-3, check_every=20, graph_iters=4) as srv:
         ids = [srv.submit(i.X, i.ybar, tol=1e-4, max_iter=400) for i in insts]
         peak_running, saw_queue = 0, False
         deadline = time.time() + 300
@@ -73,7 +73,7 @@ def test_admission_respects_the_memory_cap():
 
 def test_oversized_request_is_refused():
     inst = cr_synth.make_instance(3000, 8, "sqnorm", 0.1, 3)
-    with crgb.Server(mem_cap_bytes=1 << 20, max_active=4) as srv:
+    with crgb.Server(tile_cols=512, mem_cap_bytes=1 << 20, max_active=4) as srv:
         with pytest.raises(crgb.CRError) as e:
             srv.submit(inst.X, inst.ybar)
         assert e.value.status == 2
