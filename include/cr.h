@@ -174,8 +174,48 @@ CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
 CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, int n, double gamma, int rule, void *stream,
                                       double *L);
 
-/* Iterations taken so far. */
+/* Iterations taken so far (sweeps with CR_STEP_ADAPTIVE). */
 CR_API long long cr_iterations(const cr_ctx *ctx);
+
+/* Continuation in gamma (Section 6): changes gamma of Eq. (regularize) in place, keeping
+ * lambda^k as the warm start theta^0 of the new problem.  Recomputes L by the context's rule from
+ * the cached sigma_max(A2)^2 and the step (1/L, or upsilon/L for the adaptive rule), restarts the
+ * momentum (t = 1, as Iteration 0 of Figure "papg") and rebuilds eta(lambda^k) for the new gamma.
+ * CR_EINVAL when gamma is not finite and > 0 or when the context was created with a caller-given
+ * L (opt.lipschitz > 0), which cannot follow gamma. */
+CR_API cr_status cr_set_gamma(cr_ctx *ctx, double gamma);
+
+/* The continuation path of Section 6: for t = 0 .. stages-1, gamma_t = gammas[t] (cr_set_gamma,
+ * warm start from the previous stage) and cr_solve to rel_gap <= tols[t] with at most max_sweeps
+ * sweeps in the stage.  *out (nullable) is the record of the last stage run; CR_ENOTCONV when a
+ * stage reaches its cap (the path stops there). */
+CR_API cr_status cr_solve_path(cr_ctx *ctx, const double *gammas, const double *tols, int stages,
+                               long long max_sweeps, cr_gap_info *out);
+
+/* The continuation schedule of Section 6: for t = 1 .. stages, eps_t = eps0 / beta^t,
+ * gamma_t = kappa_gamma * eps_t and delta_t = kappa_delta * eps_t; stage t warm-starts from
+ * stage t-1 (cr_set_gamma) and iterates (checks every opt.check_every sweeps) until lambda^k
+ * passes either test of delta_t-optimality for Eq. (dual-problem):
+ *   certified:  cert_primal - dual_g <= delta_t  (a bound on max g_gamma - g_gamma(lambda^k),
+ *               since cert_primal >= p*_gamma; rigorous but loose),
+ *   practical:  |lagr_gap| <= delta_t and infeas_norm <= infeas_tol  (the duality gap
+ *               |lambda^T C eta| and normalised infeasibility of Section 5's stopping rule;
+ *               infeas_tol < 0 disables it).
+ * At most max_sweeps iterations per stage (CR_ENOTCONV, the path stops there).  Requires
+ * beta > 1 and eps0, kappa_gamma, kappa_delta > 0 (else CR_EINVAL).  *out (nullable) is the
+ * record of the last check. */
+CR_API cr_status cr_solve_continuation(cr_ctx *ctx, double eps0, double beta, double kappa_gamma,
+                                       double kappa_delta, double infeas_tol, int stages,
+                                       long long max_sweeps, cr_gap_info *out);
+
+/* Checkpoint / resume of the iteration state: the multiplier buffers, the C^T history, the
+ * vectors of eta the next sweep reads and the device scalars, as one block of
+ * cr_checkpoint_bytes(ctx) bytes in caller-owned memory (host or device).  cr_restore loads a
+ * block into a context created for the same instance and options (CR_EINVAL when its shape,
+ * precision or step rule differ); the next iterations are bitwise those of the saved run. */
+CR_API long long cr_checkpoint_bytes(const cr_ctx *ctx);
+CR_API cr_status cr_checkpoint(cr_ctx *ctx, void *buf, long long bytes);
+CR_API cr_status cr_restore(cr_ctx *ctx, const void *buf, long long bytes);
 
 /* Releases every resource of the context (NULL is ignored). */
 CR_API void cr_destroy(cr_ctx *ctx);

@@ -201,6 +201,46 @@ class Solver:
         import json
         return json.loads(cr_describe(self.ctx))
 
+    def set_gamma(self, gamma):
+        """Continuation (Section 6): new gamma, warm start from lambda^k."""
+        check(_lib().cr_set_gamma(self.ctx, float(gamma)))
+
+    def solve_path(self, gammas, tols, max_sweeps):
+        """cr_solve_path: returns (converged: bool, record of the last stage)."""
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        t = np.ascontiguousarray(tols, dtype=np.float64)
+        if g.shape != t.shape or g.ndim != 1 or g.size == 0:
+            raise ValueError("gammas and tols must be equal-length non-empty 1-D sequences")
+        rec = cr_gap_info()
+        st = _lib().cr_solve_path(self.ctx, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(g.size), int(max_sweeps),
+                                  ctypes.byref(rec))
+        if st not in (_capi.CR_OK, _capi.CR_ENOTCONV):
+            check(st)
+        return st == _capi.CR_OK, rec.as_dict()
+
+    def solve_continuation(self, eps0, beta, kappa_gamma, kappa_delta, stages, max_sweeps, infeas_tol=-1.0):
+        """cr_solve_continuation (Section 6's schedule): returns (converged: bool, last record).
+        infeas_tol >= 0 also accepts Section 5's practical test at each stage."""
+        rec = cr_gap_info()
+        st = _lib().cr_solve_continuation(self.ctx, float(eps0), float(beta), float(kappa_gamma), float(kappa_delta),
+                                          float(infeas_tol), int(stages), int(max_sweeps), ctypes.byref(rec))
+        if st not in (_capi.CR_OK, _capi.CR_ENOTCONV):
+            check(st)
+        return st == _capi.CR_OK, rec.as_dict()
+
+    def checkpoint(self):
+        """The iteration state as a host byte array (cr_checkpoint)."""
+        nb = int(_lib().cr_checkpoint_bytes(self.ctx))
+        buf = np.empty(nb, dtype=np.uint8)
+        check(_lib().cr_checkpoint(self.ctx, ctypes.c_void_p(buf.ctypes.data), nb))
+        return buf
+
+    def restore(self, buf):
+        """Loads a cr_checkpoint block into this context (same instance and options)."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(_lib().cr_restore(self.ctx, ctypes.c_void_p(b.ctypes.data), int(b.size)))
+
     def close(self):
         if self.ctx:
             cr_destroy(self.ctx)

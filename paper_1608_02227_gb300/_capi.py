@@ -99,6 +99,14 @@ _SIGS = [
     ("cr_lipschitz_noalloc", ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp,
                                             _dp]),
     ("cr_iterations", ctypes.c_longlong, [_vp]),
+    ("cr_set_gamma", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("cr_solve_path", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(cr_gap_info)]),
+    ("cr_solve_continuation", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_longlong,
+                                             ctypes.POINTER(cr_gap_info)]),
+    ("cr_checkpoint_bytes", ctypes.c_longlong, [_vp]),
+    ("cr_checkpoint", ctypes.c_int, [_vp, _vp, ctypes.c_longlong]),
+    ("cr_restore", ctypes.c_int, [_vp, _vp, ctypes.c_longlong]),
     ("cr_destroy", None, [_vp]),
     ("cr_batch_create", ctypes.c_int, [ctypes.POINTER(cr_options), _vp, ctypes.POINTER(_vp)]),
     ("cr_batch_add", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,

@@ -1,6 +1,7 @@
 // cr_api.cu -- host side of the C ABI declared in include/cr.h: context set-up, the
 // per-iteration launch sequence (sweep -> finalize/recovery), CUDA-graph replay of
 // iteration blocks, the solve loop and the result copies.
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stddef.h>
@@ -869,6 +870,238 @@ CR_API cr_status cr_lipschitz(const cr_ctx *c, double *L) {
 }
 
 CR_API long long cr_iterations(const cr_ctx *c) { return c ? c->k : -1; }
+
+namespace crh {
+
+// Rebuilds eta(lambda~^{k+1}) from the C^T history and the device beta (the commit kernel with
+// the accepted flag forced and (a,b)^k in place), after gamma or the whole state changed.
+cr_status rebuild_recovery(cr_ctx *c, const DevState &h) {
+    FinArgs f{};
+    f.N = c->N;
+    f.n = c->n;
+    f.NP = c->NP;
+    f.precision = c->opt.precision;
+    f.ldv = c->ldv;
+    f.X = c->X;
+    f.ybar = c->ybar;
+    f.a_new = c->ha[h.k & 1];
+    f.b_new = c->hb[h.k & 1];
+    for (int i = 0; i < 2; ++i) {
+        f.hist_a[i] = c->ha[i];
+        f.hist_b[i] = c->hb[i];
+    }
+    f.yh = c->yh;
+    f.yl = c->yl;
+    f.uh = c->uh;
+    f.ul = c->ul;
+    f.xiT = c->xiT;
+    f.y64 = c->y64;
+    f.u64 = c->u64;
+    f.xiT64 = c->xiT64;
+    f.xT32 = c->xT32;
+    f.xi_rm = c->xi_rm;
+    f.st = c->st;
+    CR_CUDA(launch_commit(f, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
+
+// The vectors of eta(lambda~^{k+1}) the next sweep reads (saved as they are, so that a resume
+// is bitwise: rebuilding them would add in another order).
+struct VecRef {
+    void *p;
+    size_t bytes;
+};
+int derived_vectors(const cr_ctx *c, VecRef *v) {
+    const size_t vec = (size_t)c->ldv, tvec = (size_t)c->NP * c->ldv;
+    int m = 0;
+    if (is_f64(c)) {
+        v[m++] = {c->y64, 8 * vec};
+        v[m++] = {c->u64, 8 * vec};
+        v[m++] = {c->xiT64, 8 * tvec};
+    } else {
+        v[m++] = {c->yh, 4 * 2 * vec};
+        v[m++] = {c->uh, 4 * 2 * vec};
+        v[m++] = {c->xiT, 4 * tvec};
+        if (c->xi_rm) v[m++] = {c->xi_rm, 4 * 2 * 32 * vec};
+    }
+    return m;
+}
+
+struct CkptHeader {
+    char magic[8];
+    long long N, ld, k, nbuf, tsz;
+    int n, precision, step_rule, pad;
+};
+
+}  // namespace crh
+
+CR_API cr_status cr_set_gamma(cr_ctx *c, double gamma) {
+    if (!c || !(gamma > 0.0) || !isfinite(gamma)) {
+        set_err("bad argument to cr_set_gamma");
+        return CR_EINVAL;
+    }
+    if (c->opt.lipschitz > 0.0) {
+        set_err("the context was created with a given L, which cannot follow gamma");
+        return CR_EINVAL;
+    }
+    DevState h{};
+    CR_TRY(fetch_state(c, &h));
+    const int N = c->N;
+    c->opt.gamma = gamma;
+    c->L = (c->opt.lipschitz_rule == CR_L_PAPER) ? (2.0 * N + c->a2s2) / gamma : 2.0 * N + c->a2s2 / gamma;
+    h.gamma = gamma;
+    h.inv_gamma = 1.0 / gamma;
+    h.t = 1.0;
+    h.beta = 0.0;
+    h.inv_L = 1.0 / c->L;
+    h.s = c->adaptive ? c->opt.upsilon / c->L : 1.0 / c->L;
+    h.prev_g = -DBL_MAX;
+    h.accepted = 1;
+    CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    return rebuild_recovery(c, h);
+}
+
+CR_API cr_status cr_solve_path(cr_ctx *c, const double *gammas, const double *tols, int stages,
+                               long long max_sweeps, cr_gap_info *out) {
+    if (!c || !gammas || !tols || stages < 1 || max_sweeps < 0) {
+        set_err("bad argument to cr_solve_path");
+        return CR_EINVAL;
+    }
+    for (int t = 0; t < stages; ++t) {
+        if (gammas[t] != c->opt.gamma) CR_TRY(cr_set_gamma(c, gammas[t]));
+        cr_gap_info g{};
+        const cr_status s = cr_solve(c, tols[t], c->k + max_sweeps, &g);
+        if (out) *out = g;
+        if (s != CR_OK) return s;
+    }
+    return CR_OK;
+}
+
+CR_API cr_status cr_solve_continuation(cr_ctx *c, double eps0, double beta, double kappa_gamma,
+                                       double kappa_delta, double infeas_tol, int stages,
+                                       long long max_sweeps, cr_gap_info *out) {
+    if (!c || !(eps0 > 0.0) || !(beta > 1.0) || !(kappa_gamma > 0.0) || !(kappa_delta > 0.0) || stages < 1 ||
+        max_sweeps < 0 || !isfinite(eps0 * kappa_gamma * kappa_delta * beta) || isnan(infeas_tol)) {
+        set_err("bad argument to cr_solve_continuation");
+        return CR_EINVAL;
+    }
+    double eps = eps0;
+    for (int t = 1; t <= stages; ++t) {
+        eps /= beta;  // eps_t = eps0 / beta^t
+        const double gamma_t = kappa_gamma * eps, delta_t = kappa_delta * eps;
+        if (!(gamma_t > 0.0)) {
+            set_err("gamma underflows at stage %d", t);
+            return CR_EINVAL;
+        }
+        CR_TRY(cr_set_gamma(c, gamma_t));
+        const long long cap = c->k + max_sweeps;
+        cr_gap_info g{};
+        for (;;) {
+            CR_TRY(cr_gap(c, &g));
+            if (out) *out = g;
+            // cert_primal >= p*_gamma = max g_gamma, so this gap bounds the dual suboptimality
+            const bool certified = g.cert_primal - g.dual_g <= delta_t;
+            // Section 5's test: |lambda^T C eta| and the normalised infeasibility
+            const bool practical = fabs(g.lagr_gap) <= delta_t && g.infeas_norm <= infeas_tol;
+            if (c->k > 0 && (certified || practical)) break;
+            if (c->k >= cap) {
+                set_err("stage %d: gap %.3e / certified %.3e > delta_t %.3e after %lld sweeps", t,
+                        fabs(g.lagr_gap), g.cert_primal - g.dual_g, delta_t, max_sweeps);
+                return CR_ENOTCONV;
+            }
+            CR_TRY(cr_dual_step(c, (int)std::min<long long>(c->opt.check_every, cap - c->k)));
+        }
+    }
+    return CR_OK;
+}
+
+CR_API long long cr_checkpoint_bytes(const cr_ctx *c) {
+    if (!c) return -1;
+    const long long tsz = is_f64(c) ? 8 : 4, nbuf = c->adaptive ? 3 : 2;
+    VecRef v[4];
+    long long vb = 0;
+    for (int i = 0, m = derived_vectors(c, v); i < m; ++i) vb += (long long)v[i].bytes;
+    return (long long)sizeof(CkptHeader) + (long long)sizeof(DevState) + nbuf * c->N * c->ld * tsz +
+           2 * 8LL * c->N * (c->n + 1) + vb;
+}
+
+CR_API cr_status cr_checkpoint(cr_ctx *c, void *buf, long long bytes) {
+    if (!c || !buf || bytes < cr_checkpoint_bytes(c)) {
+        set_err("bad argument to cr_checkpoint");
+        return CR_EINVAL;
+    }
+    CkptHeader hd{};
+    memcpy(hd.magic, "CRCKPT01", 8);
+    hd.N = c->N;
+    hd.ld = c->ld;
+    hd.k = c->k;
+    hd.nbuf = c->adaptive ? 3 : 2;
+    hd.tsz = is_f64(c) ? 8 : 4;
+    hd.n = c->n;
+    hd.precision = c->opt.precision;
+    hd.step_rule = c->opt.step_rule;
+    char *p = (char *)buf;
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    CR_CUDA(cudaMemcpy(p, &hd, sizeof(hd), cudaMemcpyDefault));
+    p += sizeof(hd);
+    CR_CUDA(cudaMemcpyAsync(p, c->st, sizeof(DevState), cudaMemcpyDefault, c->stream));
+    p += sizeof(DevState);
+    const size_t lb = (size_t)c->N * c->ld * hd.tsz;
+    for (int i = 0; i < hd.nbuf; ++i, p += lb) CR_CUDA(cudaMemcpyAsync(p, c->lam[i], lb, cudaMemcpyDefault, c->stream));
+    for (int i = 0; i < 2; ++i) {
+        CR_CUDA(cudaMemcpyAsync(p, c->ha[i], 8 * (size_t)c->N, cudaMemcpyDefault, c->stream));
+        p += 8 * (size_t)c->N;
+        CR_CUDA(cudaMemcpyAsync(p, c->hb[i], 8 * (size_t)c->N * c->n, cudaMemcpyDefault, c->stream));
+        p += 8 * (size_t)c->N * c->n;
+    }
+    VecRef v[4];
+    for (int i = 0, m = derived_vectors(c, v); i < m; p += v[i].bytes, ++i)
+        CR_CUDA(cudaMemcpyAsync(p, v[i].p, v[i].bytes, cudaMemcpyDefault, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
+
+CR_API cr_status cr_restore(cr_ctx *c, const void *buf, long long bytes) {
+    if (!c || !buf || bytes < cr_checkpoint_bytes(c)) {
+        set_err("bad argument to cr_restore");
+        return CR_EINVAL;
+    }
+    CkptHeader hd{};
+    const char *p = (const char *)buf;
+    CR_CUDA(cudaMemcpy(&hd, p, sizeof(hd), cudaMemcpyDefault));
+    p += sizeof(hd);
+    if (memcmp(hd.magic, "CRCKPT01", 8) != 0 || hd.N != c->N || hd.n != c->n || hd.ld != c->ld ||
+        hd.precision != c->opt.precision || hd.step_rule != c->opt.step_rule ||
+        hd.nbuf != (c->adaptive ? 3 : 2) || hd.tsz != (is_f64(c) ? 8 : 4)) {
+        set_err("the checkpoint belongs to another instance shape, precision or step rule");
+        return CR_EINVAL;
+    }
+    DevState h{};
+    CR_CUDA(cudaMemcpy(&h, p, sizeof(DevState), cudaMemcpyDefault));
+    p += sizeof(DevState);
+    const size_t lb = (size_t)c->N * c->ld * hd.tsz;
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < hd.nbuf; ++i, p += lb) CR_CUDA(cudaMemcpyAsync(c->lam[i], p, lb, cudaMemcpyDefault, c->stream));
+    for (int i = 0; i < 2; ++i) {
+        CR_CUDA(cudaMemcpyAsync(c->ha[i], p, 8 * (size_t)c->N, cudaMemcpyDefault, c->stream));
+        p += 8 * (size_t)c->N;
+        CR_CUDA(cudaMemcpyAsync(c->hb[i], p, 8 * (size_t)c->N * c->n, cudaMemcpyDefault, c->stream));
+        p += 8 * (size_t)c->N * c->n;
+    }
+    VecRef v[4];
+    for (int i = 0, m = derived_vectors(c, v); i < m; p += v[i].bytes, ++i)
+        CR_CUDA(cudaMemcpyAsync(v[i].p, p, v[i].bytes, cudaMemcpyDefault, c->stream));
+    // the saved context's gamma and L (a restore also carries a continuation stage)
+    c->opt.gamma = h.gamma;
+    c->L = 1.0 / (c->adaptive ? h.inv_L : h.s);
+    c->k = hd.k;
+    h.fin_counter = 0u;
+    h.cert_counter = 0u;
+    CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    return CR_OK;
+}
 
 CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
     if (!c || !buf || len <= 0) {

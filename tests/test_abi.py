@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every entry point declared in include/*.h
 (CPU only: no compute call is made without a GPU)."""
+import ctypes
 import glob
 import os
 import re
@@ -56,6 +57,14 @@ def test_host_only_calls(lib):
     assert lib.cr_strerror(1) == b"invalid argument"
     with pytest.raises(TypeError):
         crgb.default_options(no_such_option=1)
+    # argument checks that return before any CUDA call
+    assert lib.cr_checkpoint_bytes(None) == -1
+    assert lib.cr_set_gamma(None, 1e-3) == 1
+    assert lib.cr_checkpoint(None, None, 0) == 1
+    assert lib.cr_restore(None, None, 0) == 1
+    g = (ctypes.c_double * 1)(1e-3)
+    assert lib.cr_solve_path(None, g, g, 1, 10, None) == 1
+    assert lib.cr_solve_continuation(None, 0.1, 2.0, 0.1, 0.1, -1.0, 2, 10, None) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path):
