@@ -64,7 +64,9 @@ typedef enum {
     CR_L_PAPER = 1       /* L = (2N + sigma_max(A2)^2) / gamma >= sigma_max(C)^2 / gamma, Eq. (lischitz) */
 } cr_lipschitz_rule;
 
-#define CR_MAX_N 32      /* largest point dimension n supported by the kernels */
+#define CR_MAX_N 128     /* largest point dimension n supported by the kernels (FP64, FP32) */
+#define CR_MAX_N_TF32 31 /* CR_MIXED_TF32 (the tensor-core sweep) */
+#define CR_MAX_N_BATCH 32 /* cr_batch_* and cr_server_* instances */
 
 /* Step size of Step 2 of Figure "papg".
  *   CR_STEP_CONSTANT: 1/L every iteration.
@@ -165,7 +167,7 @@ CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
  *   X: N x n points, FP64, row-major, DEVICE memory only (host pointers are rejected with
  *   CR_EINVAL); rule: CR_L_HESSIAN or CR_L_PAPER; stream: cudaStream_t or NULL; *L receives
  *   the same value cr_create computes for these inputs.  Synchronises the stream.
- * Limit: 1 <= n <= CR_MAX_N (32); the scratch is a fixed 16.6 KB array in device memory that
+ * Limit: 1 <= n <= CR_MAX_N (128); the scratch is a fixed 264 KB array in device memory that
  * every GPU which loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating call is made.  The first call on a device (with that device current)
  * looks up the array's device address; make that first call before any stream capture.
@@ -236,7 +238,7 @@ typedef struct cr_batch cr_batch;
  * cr_batch_run).  stream: as in cr_create. */
 CR_API cr_status cr_batch_create(const cr_options *opt, void *stream, cr_batch **out);
 
-/* Adds one instance (X: N x n, ybar: N; host or device; copied).  It is retired once a
+/* Adds one instance (X: N x n with n <= CR_MAX_N_BATCH, ybar: N; host or device; copied).  It is retired once a
  * check finds rel_gap <= rel_gap_tol (status CR_OK) or after max_iter iterations
  * (status CR_ENOTCONV).  *id receives its handle (>= 0). */
 CR_API cr_status cr_batch_add(cr_batch *b, const double *X, const double *ybar, long long N, int n,
@@ -296,8 +298,8 @@ typedef struct cr_serve_stats {
 CR_API cr_status cr_server_create(const cr_options *opt, long long mem_cap_bytes, int max_active, void *stream,
                                   cr_server **out);
 
-/* Queues one solve of Eq. (regularize) (inputs copied before returning; host or device).
- * CR_ENOMEM if the instance alone exceeds the memory cap. */
+/* Queues one solve of Eq. (regularize) (inputs copied before returning; host or device;
+ * n <= CR_MAX_N_BATCH).  CR_ENOMEM if the instance alone exceeds the memory cap. */
 CR_API cr_status cr_server_submit(cr_server *s, const double *X, const double *ybar, long long N, int n,
                                   double rel_gap_tol, long long max_iter, long long *req_id);
 

@@ -16,7 +16,9 @@ CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ENUMERIC, CR
 CR_FP64, CR_FP32, CR_MIXED_TF32 = 0, 1, 2
 CR_L_HESSIAN, CR_L_PAPER = 0, 1
 CR_STEP_CONSTANT, CR_STEP_ADAPTIVE = 0, 1
-CR_MAX_N = 32
+CR_MAX_N = 128
+CR_MAX_N_TF32 = 31
+CR_MAX_N_BATCH = 32
 
 
 class cr_options(ctypes.Structure):

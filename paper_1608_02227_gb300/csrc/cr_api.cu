@@ -148,6 +148,9 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.st = c->st;
         a.rowpart = (float *)c->rowpart;
         a.colpart = (float *)c->colpart;
+        a.adaptive = c->adaptive ? 1 : 0;
+        for (int i = 0; i < 3; ++i) a.B[i] = (float *)c->lam[i];
+        a.dpart = (float *)c->dpart;
         CR_CUDA(launch_sweep_f(c->NP, a, c->grid, c->stream));
     }
     if (e1) CR_CUDA(cudaEventRecord(e1, c->stream));
@@ -265,7 +268,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     // (same arithmetic, loads through registers) for A/B measurements.
     const char *variant = getenv("CR_SWEEP");
     c->tc = c->opt.precision == CR_MIXED_TF32;
-    c->tma = !f64 && !c->tc && !(variant && strcmp(variant, "simple") == 0);
+    c->tma = !f64 && !c->tc && c->NP <= 32 && !(variant && strcmp(variant, "simple") == 0);
     c->rows = c->tc ? sweep_tc_rows() : (c->tma ? sweep_tma_rows(c->NP) : cfg.rows);
     c->RB = (N + c->rows - 1) / c->rows;
     if (c->tc)
@@ -282,7 +285,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         return CR_EUNSUPPORTED;
     }
     choose_split(c);
-    if (c->adaptive && !f64 && !c->tc && !c->tma) {
+    if (c->adaptive && !f64 && !c->tc && !c->tma && c->NP <= 32) {
         set_err("the adaptive step needs the TMA, tensor-core or FP64 sweep (CR_SWEEP=simple has none)");
         return CR_EUNSUPPORTED;
     }
@@ -644,7 +647,7 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
         set_err("unknown precision %d", o.precision);
         return CR_EINVAL;
     }
-    if (o.precision == CR_MIXED_TF32 && n > 31) {
+    if (o.precision == CR_MIXED_TF32 && n > CR_MAX_N_TF32) {
         set_err("CR_MIXED_TF32 handles n <= 31 (a row of ones joins the 32-wide operand)");
         return CR_EUNSUPPORTED;
     }
@@ -1119,7 +1122,8 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
              pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters, c->opt.step_rule,
              c->opt.upsilon,
-             c->tc ? "tcgen05" : (c->tma ? "tma" : (is_f64(c) ? "fp64" : "simple")));
+             c->tc ? "tcgen05"
+                   : (c->tma ? "tma" : (c->NP > 32 ? (is_f64(c) ? "wide-fp64" : "wide-fp32") : (is_f64(c) ? "fp64" : "simple"))));
     return CR_OK;
 }
 

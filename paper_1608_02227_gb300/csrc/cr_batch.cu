@@ -383,6 +383,10 @@ CR_API cr_status cr_batch_add(cr_batch *b, const double *X, const double *ybar, 
         set_err("bad argument to cr_batch_add");
         return CR_EINVAL;
     }
+    if (n > CR_MAX_N_BATCH) {
+        set_err("batched instances have n <= %d (n = %d)", CR_MAX_N_BATCH, n);
+        return CR_EINVAL;
+    }
     cr_options o = b->opt;
     o.tile_cols = kMinSplit;  // row partials sized for the narrowest split the batch may use
     o.graph_iters = 0;
@@ -453,7 +457,7 @@ CR_API cr_status cr_batch_remove(cr_batch *b, int id) {
 }
 
 CR_API long long cr_batch_instance_bytes(long long N, int n) {
-    if (N < 2 || n < 1 || n > CR_MAX_N) return -1;
+    if (N < 2 || n < 1 || n > CR_MAX_N_BATCH) return -1;
     const long long ld = round_up(N, 32), ldv = round_up(N, kChunk);
     const long long NP = bucket_np(n);
     const long long RB = (N + 31) / 32, S = (ld + kMinSplit - 1) / kMinSplit;

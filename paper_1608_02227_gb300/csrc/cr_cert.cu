@@ -13,6 +13,8 @@
 // are combined in increasing row order (deterministic).
 #include <math.h>
 
+#include <type_traits>
+
 #include "cr_internal.cuh"
 
 namespace cr {
@@ -159,6 +161,124 @@ __global__ void __launch_bounds__(kCT) cert_pass_f64(const CertArgs a) {
     }
 }
 
+// Wide points (NP > 32): x_j no longer fits in registers next to the row loop, so the
+// dot products of a 32-row tile are accumulated over components in chunks of 16 (x_j of the
+// chunk in registers, xi of the tile read as 16-byte broadcasts); the order of the sum over
+// k is the same as above.
+constexpr int kRW = 32;  // rows per tile (wide)
+constexpr int kKC = 16;  // components per register chunk (NP is a multiple of 16)
+
+template <typename T>
+__global__ void __launch_bounds__(kCT) cert_pass_wide(const CertArgs a) {
+    constexpr bool F32 = std::is_same<T, float>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sxi = reinterpret_cast<T *>(smem_raw);  // [NP][kRW]
+    T *su0 = sxi + (size_t)a.NP * kRW;          // [kRW] u (FP32: hi)
+    T *su1 = su0 + kRW;                         // [kRW] FP32: u lo
+    const T *xT = F32 ? (const T *)a.xT32 : (const T *)a.xT64;
+    const T *xiT = F32 ? (const T *)a.xiT : (const T *)a.xiT64;
+    const T *u0 = F32 ? (const T *)a.uh : (const T *)a.u64;
+    const T *u1 = F32 ? (const T *)a.ul : (const T *)a.u64;
+    const T *y0 = F32 ? (const T *)a.yh : (const T *)a.y64;
+    const T *y1 = F32 ? (const T *)a.yl : (const T *)a.y64;
+    const int j = blockIdx.x * kCT + threadIdx.x;
+    const bool jv = j < a.N;
+    const int rs = blockIdx.y;
+    const int rows_per = (a.N + a.row_splits - 1) / a.row_splits;
+    const int r0 = rs * rows_per, r1 = min(a.N, r0 + rows_per);
+    const T yj0 = jv ? y0[j] : (T)0, yj1 = (F32 && jv) ? y1[j] : (T)0;
+    T best = (T)-INFINITY;
+    int arg = -1;
+    double inf = 0.0;
+    for (int t0 = r0; t0 < r1; t0 += kRW) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < kRW * (a.NP + 2); q += kCT) {
+            const int c = q / kRW, r = q - c * kRW, i = t0 + r;
+            const bool ok = i < r1;
+            if (c < a.NP)
+                sxi[c * kRW + r] = ok ? xiT[(long long)c * a.ldv + i] : (T)0;
+            else if (c == a.NP)
+                su0[r] = ok ? u0[i] : (T)0;
+            else
+                su1[r] = (F32 && ok) ? u1[i] : (T)0;
+        }
+        __syncthreads();
+        T d[kRW];
+#pragma unroll
+        for (int r = 0; r < kRW; ++r) d[r] = (T)0;
+        for (int kc = 0; kc < a.NP; kc += kKC) {
+            T xj[kKC];
+#pragma unroll
+            for (int k = 0; k < kKC; ++k) xj[k] = jv ? xT[(long long)(kc + k) * a.ldv + j] : (T)0;
+#pragma unroll
+            for (int k = 0; k < kKC; ++k) {
+                const T *row = sxi + (kc + k) * kRW;
+#pragma unroll
+                for (int r = 0; r < kRW; r += 16 / sizeof(T)) {
+                    if constexpr (F32) {
+                        const float4 v = *reinterpret_cast<const float4 *>(row + r);
+                        d[r + 0] = fmaf(v.x, (float)xj[k], (float)d[r + 0]);
+                        d[r + 1] = fmaf(v.y, (float)xj[k], (float)d[r + 1]);
+                        d[r + 2] = fmaf(v.z, (float)xj[k], (float)d[r + 2]);
+                        d[r + 3] = fmaf(v.w, (float)xj[k], (float)d[r + 3]);
+                    } else {
+                        const double2 v = *reinterpret_cast<const double2 *>(row + r);
+                        d[r + 0] = fma(v.x, (double)xj[k], (double)d[r + 0]);
+                        d[r + 1] = fma(v.y, (double)xj[k], (double)d[r + 1]);
+                    }
+                }
+            }
+        }
+        const int cnt = min(kRW, r1 - t0);
+        float infs = 0.f;  // FP32: per tile, then added in FP64 (as the narrow pass)
+#pragma unroll
+        for (int r = 0; r < kRW; ++r) {
+            if (r >= cnt) break;
+            // v_ij - y_j (FP32: hi and lo parts of u_i - y_j subtracted separately)
+            T v;
+            if constexpr (F32)
+                v = ((su0[r] - yj0) + (su1[r] - yj1)) + d[r];
+            else
+                v = (su0[r] - yj0) + d[r];
+            const int i = t0 + r;
+            if (i != j) {
+                if (v > best) {
+                    best = v;
+                    arg = i;
+                }
+                if (v > (T)0) {
+                    if constexpr (F32)
+                        infs = fmaf(v, v, infs);
+                    else
+                        inf = fma(v, v, inf);
+                }
+            }
+        }
+        if constexpr (F32) inf += (double)infs;
+    }
+    if (jv) {
+        const long long o = (long long)rs * a.N + j;
+        a.pmax[o] = (double)best;
+        a.parg[o] = arg;
+        a.pinf[o] = inf;
+    }
+}
+
+size_t cert_wide_smem(int NP, bool f64) { return (f64 ? 8 : 4) * ((size_t)NP * kRW + 2 * kRW); }
+
+template <typename T>
+cudaError_t run_cert_wide(const CertArgs &a, dim3 grid, cudaStream_t s) {
+    const size_t sm = cert_wide_smem(CR_MAX_N, sizeof(T) == 8);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(cert_pass_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cert_pass_wide<T><<<grid, kCT, cert_wide_smem(a.NP, sizeof(T) == 8), s>>>(a);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kCT) cert_combine_kernel(const CertArgs a) {
     const int j = blockIdx.x * kCT + threadIdx.x;
     DevState *st = a.st;
@@ -246,7 +366,11 @@ cudaError_t launch_cert(const CertArgs &a, cudaStream_t s) {
     const unsigned gN = (unsigned)((a.N + kCT - 1) / kCT);
     cert_prep_kernel<<<gN, kCT, 0, s>>>(a);
     dim3 grid(gN, (unsigned)a.row_splits);
-    if (a.precision == CR_FP64) {
+    if (a.NP > 32) {
+        if (a.NP > CR_MAX_N || a.NP % kKC != 0) return cudaErrorInvalidValue;
+        const cudaError_t e = a.precision == CR_FP64 ? run_cert_wide<double>(a, grid, s) : run_cert_wide<float>(a, grid, s);
+        if (e != cudaSuccess) return e;
+    } else if (a.precision == CR_FP64) {
         switch (a.NP) {
 #define CASE(V) \
     case V: cert_pass_f64<V><<<grid, kCT, 0, s>>>(a); break;

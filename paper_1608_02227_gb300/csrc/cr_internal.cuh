@@ -73,6 +73,7 @@ inline int bucket_np(int n) {
     static const int b[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
     for (int v : b)
         if (n <= v) return v;
+    if (n <= CR_MAX_N) return (n + 15) / 16 * 16;  // wide points: the sweep of cr_sweep_wide.cu
     return -1;
 }
 
@@ -82,6 +83,9 @@ inline long long round_up(long long a, long long m) { return (a + m - 1) / m * m
 struct SweepArgsF {
     const float *P;          // lambda^{k-1}
     float *Q;                // lambda^{k-2} in, lambda^k out
+    float *B[3];             // adaptive step (wide points only): the three multiplier buffers
+    int adaptive;
+    float *dpart;            // adaptive step: S x N row sums of (lambda^k - lambda~^k)^2
     long long ld;            // leading dimension of P, Q
     int N;
     int row_blocks;          // RB = ceil(N / ROWS)
@@ -131,6 +135,13 @@ cudaError_t launch_sweep_f(int np, const SweepArgsF &a, int grid, cudaStream_t s
 cudaError_t launch_sweep_d(int np, const SweepArgsD &a, int grid, cudaStream_t s);
 cudaError_t sweep_occupancy_f(int np, int *blocks_per_sm);
 cudaError_t sweep_occupancy_d(int np, int *blocks_per_sm);
+
+// Wide points, 32 < NP <= CR_MAX_N, NP a multiple of 16 (cr_sweep_wide.cu); the plain
+// FP32/FP64 entry points above route such NP here.  Both support the adaptive step.
+bool sweep_wide_config(int np, bool f64, SweepConfig *cfg);
+cudaError_t launch_sweep_wide_f(int np, const SweepArgsF &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep_wide_d(int np, const SweepArgsD &a, int grid, cudaStream_t s);
+cudaError_t sweep_wide_occupancy(int np, bool f64, bool adaptive, int *blocks_per_sm);
 
 // FP32 sweep with the TMA / mbarrier pipeline (cr_sweep_tma.cu)
 struct TmaSweepArgs {

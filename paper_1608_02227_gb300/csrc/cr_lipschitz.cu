@@ -63,26 +63,31 @@ __global__ void scatter_kernel(const double *X, int N, int n, const double *mean
     }
 }
 
-// Jacobi eigendecomposition of the n x n symmetric Sc by one warp, parallel ordering:
-// each sweep has m-1 rounds (m = n rounded up to even) of m/2 disjoint pairs (circle
-// schedule); lane i computes the rotation of pair i, then lane r applies all rotations of
-// the round to row/column r of A and to row r of V.  D (n) and V (n x n, columns =
-// eigenvectors) are written at the end.
-__global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
-    __shared__ double A[CR_MAX_N * CR_MAX_N];
-    __shared__ double Q[CR_MAX_N * CR_MAX_N];
+// Jacobi eigendecomposition of the n x n symmetric Sc by one block of kJT threads, parallel
+// ordering: each sweep has m-1 rounds (m = n rounded up to even) of m/2 disjoint pairs (circle
+// schedule); thread i computes the rotation of pair i, then thread r applies all rotations of
+// the round to row/column r of A and to row r of V.  A lives in dynamic shared memory
+// (n^2 doubles), the rotations accumulate directly in V (n x n, columns = eigenvectors);
+// D (n) is written at the end.
+constexpr int kJT = CR_MAX_N;  // one thread per row, and at least m/2 threads
+static_assert(kJT % 32 == 0 && kJT >= 32, "whole warps");
+
+__global__ void __launch_bounds__(kJT) jacobi_kernel(const double *Sc, int n, double *D, double *V) {
+    extern __shared__ double A[];  // n x n
     __shared__ double rc[CR_MAX_N / 2], rs[CR_MAX_N / 2];
     __shared__ int rp[CR_MAX_N / 2], rq[CR_MAX_N / 2];
-    const int lane = threadIdx.x;
+    __shared__ double red[2][kJT / 32];
+    __shared__ int done;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int m = (n + 1) & ~1;
-    for (int i = lane; i < n * n; i += 32) {
+    for (int i = t; i < n * n; i += kJT) {
         A[i] = Sc[i];
-        Q[i] = (i / n == i % n) ? 1.0 : 0.0;
+        V[i] = (i / n == i % n) ? 1.0 : 0.0;
     }
-    __syncwarp();
+    __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0, dia = 0.0;
-        for (int i = lane; i < n * n; i += 32) {
+        for (int i = t; i < n * n; i += kJT) {
             const int p = i / n, q = i % n;
             if (p == q)
                 dia += A[i] * A[i];
@@ -93,63 +98,76 @@ __global__ void jacobi_kernel(const double *Sc, int n, double *D, double *V) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             dia += __shfl_xor_sync(0xffffffffu, dia, o);
         }
-        if (off <= 1e-32 * dia || off == 0.0) break;
+        if (lane == 0) {
+            red[0][warp] = off;
+            red[1][warp] = dia;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int w = 0; w < kJT / 32; ++w) {
+                so += red[0][w];
+                sd += red[1][w];
+            }
+            done = (so <= 1e-32 * sd || so == 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (done) break;
         for (int round = 0; round < m - 1; ++round) {
-            if (lane < m / 2) {
+            if (t < m / 2) {
                 // circle method: position 0 fixed, the others rotate by `round`
-                const int a0 = lane == 0 ? 0 : ((lane - 1 + round) % (m - 1)) + 1;
-                const int b0 = ((m - 1 - lane - 1 + round) % (m - 1)) + 1;
+                const int a0 = t == 0 ? 0 : ((t - 1 + round) % (m - 1)) + 1;
+                const int b0 = ((m - 1 - t - 1 + round) % (m - 1)) + 1;
                 const int p = min(a0, b0), q = max(a0, b0);
                 double c = 1.0, sn = 0.0;
                 if (q < n) {
                     const double apq = A[p * n + q];
                     if (apq != 0.0) {
                         const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        sn = t * c;
+                        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        sn = tt * c;
                     }
                 }
-                rp[lane] = p;
-                rq[lane] = q;
-                rc[lane] = c;
-                rs[lane] = sn;
+                rp[t] = p;
+                rq[t] = q;
+                rc[t] = c;
+                rs[t] = sn;
             }
-            __syncwarp();
-            if (lane < n) {  // A <- A J and V <- V J: row `lane`, all pairs of the round
+            __syncthreads();
+            if (t < n) {  // A <- A J and V <- V J: row t, all pairs of the round
                 for (int i = 0; i < m / 2; ++i) {
                     const int p = rp[i], q = rq[i];
                     if (q >= n || rs[i] == 0.0) continue;
                     const double c = rc[i], sn = rs[i];
-                    const double arp = A[lane * n + p], arq = A[lane * n + q];
-                    A[lane * n + p] = c * arp - sn * arq;
-                    A[lane * n + q] = sn * arp + c * arq;
-                    const double qrp = Q[lane * n + p], qrq = Q[lane * n + q];
-                    Q[lane * n + p] = c * qrp - sn * qrq;
-                    Q[lane * n + q] = sn * qrp + c * qrq;
+                    const double arp = A[t * n + p], arq = A[t * n + q];
+                    A[t * n + p] = c * arp - sn * arq;
+                    A[t * n + q] = sn * arp + c * arq;
+                    const double qrp = V[t * n + p], qrq = V[t * n + q];
+                    V[t * n + p] = c * qrp - sn * qrq;
+                    V[t * n + q] = sn * qrp + c * qrq;
                 }
             }
-            __syncwarp();
-            if (lane < n) {  // A <- J^T A: column `lane`, all pairs of the round
+            __syncthreads();
+            if (t < n) {  // A <- J^T A: column t, all pairs of the round
                 for (int i = 0; i < m / 2; ++i) {
                     const int p = rp[i], q = rq[i];
                     if (q >= n || rs[i] == 0.0) continue;
                     const double c = rc[i], sn = rs[i];
-                    const double apr = A[p * n + lane], aqr = A[q * n + lane];
-                    A[p * n + lane] = c * apr - sn * aqr;
-                    A[q * n + lane] = sn * apr + c * aqr;
+                    const double apr = A[p * n + t], aqr = A[q * n + t];
+                    A[p * n + t] = c * apr - sn * aqr;
+                    A[q * n + t] = sn * apr + c * aqr;
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
-    for (int i = lane; i < n; i += 32) D[i] = A[i * n + i];
-    for (int i = lane; i < n * n; i += 32) V[i] = Q[i];
+    for (int i = t; i < n; i += kJT) D[i] = A[i * n + i];
 }
 
 __global__ void secular_kernel(const double *X, int N, int n, const double *mean, const double *D,
                                const double *V, unsigned long long *best_bits) {
-    __shared__ double sV[CR_MAX_N * CR_MAX_N];
+    extern __shared__ double sV[];  // n x n eigenvectors
     __shared__ double sD[CR_MAX_N];
     __shared__ double smean[CR_MAX_N];
     for (int i = threadIdx.x; i < n * n; i += kT) sV[i] = V[i];
@@ -239,6 +257,24 @@ __global__ void secular_kernel(const double *X, int N, int n, const double *mean
     if (threadIdx.x == 0) atomicMax(best_bits, (unsigned long long)__double_as_longlong(sm[0]));
 }
 
+// The two kernels with n^2 doubles of dynamic shared memory (up to 128 KB at n = 128).
+cudaError_t launch_eig_and_secular(const double *X, int N, int n, const double *mean, const double *Sc, double *D,
+                                   double *V, unsigned long long *best, cudaStream_t s) {
+    static bool attr_set = false;  // per process; the attribute is per device function
+    const int big = (int)(sizeof(double) * CR_MAX_N * CR_MAX_N);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const size_t sm = sizeof(double) * (size_t)n * n;
+    jacobi_kernel<<<1, kJT, sm, s>>>(Sc, n, D, V);
+    secular_kernel<<<(unsigned)((N + kT - 1) / kT), kT, sm, s>>>(X, N, n, mean, D, V, best);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStream_t s) {
@@ -251,10 +287,9 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
     cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     mean_kernel<<<n, kT, 0, s>>>(X, N, n, mean);
     scatter_kernel<<<n * (n + 1) / 2, kT, 0, s>>>(X, N, n, mean, Sc);
-    jacobi_kernel<<<1, 32, 0, s>>>(Sc, n, D, V);  // one warp
-    secular_kernel<<<(N + kT - 1) / kT, kT, 0, s>>>(X, N, n, mean, D, V, best);
+    e = launch_eig_and_secular(X, N, n, mean, Sc, D, V, best, s);
     unsigned long long bits = 0;
-    e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return e;
@@ -280,7 +315,7 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
 namespace {
 
 // mean (n) + scatter (n^2) + eigenvectors (n^2) + eigenvalues (n) + one 64-bit max word,
-// for n <= CR_MAX_N: 2 * 32 * 32 + 2 * 32 + 8 doubles = 16.6 KB.
+// for n <= CR_MAX_N: 2 * 128 * 128 + 2 * 128 + 8 doubles = 264 KB.
 constexpr int kLipScratchDoubles = 2 * CR_MAX_N * CR_MAX_N + 2 * CR_MAX_N + 8;
 static __device__ __align__(256) double g_lip_scratch[kLipScratchDoubles];
 
@@ -345,9 +380,7 @@ extern "C" CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, i
     if (e == cudaSuccess) {
         mean_kernel<<<n, kT, 0, s>>>(X, (int)N, n, mean);
         scatter_kernel<<<n * (n + 1) / 2, kT, 0, s>>>(X, (int)N, n, mean, Sc);
-        jacobi_kernel<<<1, 32, 0, s>>>(Sc, n, D, V);
-        secular_kernel<<<(unsigned)((N + kT - 1) / kT), kT, 0, s>>>(X, (int)N, n, mean, D, V, best);
-        e = cudaGetLastError();
+        e = cr::launch_eig_and_secular(X, (int)N, n, mean, Sc, D, V, best, s);
     }
     unsigned long long bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);

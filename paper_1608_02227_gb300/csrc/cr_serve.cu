@@ -226,7 +226,7 @@ CR_API cr_status cr_server_create(const cr_options *opt, long long mem_cap_bytes
 
 CR_API cr_status cr_server_submit(cr_server *s, const double *X, const double *ybar, long long N, int n,
                                   double rel_gap_tol, long long max_iter, long long *req_id) {
-    if (!s || !X || !ybar || !req_id || N < 2 || N > (1LL << 30) || n < 1 || n > CR_MAX_N ||
+    if (!s || !X || !ybar || !req_id || N < 2 || N > (1LL << 30) || n < 1 || n > CR_MAX_N_BATCH ||
         !(rel_gap_tol >= 0.0) || max_iter < 0) {
         set_err("bad argument to cr_server_submit");
         return CR_EINVAL;

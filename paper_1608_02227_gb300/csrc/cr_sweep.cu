@@ -472,6 +472,7 @@ cudaError_t dispatch_d(int np, const SweepArgsD *a, int grid, cudaStream_t st, i
 }  // namespace
 
 bool sweep_config_f(int np, SweepConfig *cfg) {
+    if (np > 32) return sweep_wide_config(np, false, cfg);
     switch (np) {
 #define CASE(V)                                                            \
     case V:                                                                \
@@ -486,6 +487,7 @@ bool sweep_config_f(int np, SweepConfig *cfg) {
 }
 
 bool sweep_config_d(int np, SweepConfig *cfg) {
+    if (np > 32) return sweep_wide_config(np, true, cfg);
     switch (np) {
 #define CASE(V)                                                            \
     case V:                                                                \
@@ -500,15 +502,19 @@ bool sweep_config_d(int np, SweepConfig *cfg) {
 }
 
 cudaError_t launch_sweep_f(int np, const SweepArgsF &a, int grid, cudaStream_t s) {
+    if (np > 32) return launch_sweep_wide_f(np, a, grid, s);
     return dispatch_f(np, &a, grid, s, nullptr);
 }
 cudaError_t launch_sweep_d(int np, const SweepArgsD &a, int grid, cudaStream_t s) {
+    if (np > 32) return launch_sweep_wide_d(np, a, grid, s);
     return dispatch_d(np, &a, grid, s, nullptr);
 }
 cudaError_t sweep_occupancy_f(int np, int *blocks_per_sm) {
+    if (np > 32) return sweep_wide_occupancy(np, false, false, blocks_per_sm);
     return dispatch_f(np, nullptr, 0, 0, blocks_per_sm);
 }
 cudaError_t sweep_occupancy_d(int np, int *blocks_per_sm) {
+    if (np > 32) return sweep_wide_occupancy(np, true, false, blocks_per_sm);
     return dispatch_d(np, nullptr, 0, 0, blocks_per_sm);
 }
 

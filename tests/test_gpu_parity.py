@@ -168,14 +168,14 @@ def test_solve_reaches_tolerance_like_oracle():
     assert abs(rec["primal_r"] - log["r"][-1]) <= 1e-9 * abs(log["r"][-1])
 
 
-@pytest.mark.parametrize("bad", ["N1", "n33", "gamma0", "nanX", "infy", "odd_graph"])
+@pytest.mark.parametrize("bad", ["N1", "n_over", "gamma0", "nanX", "infy", "odd_graph"])
 def test_invalid_inputs_are_rejected(bad):
     inst = cr_synth.make_instance(10, 2, "sqnorm", 0.1, 0)
     X, y, kw = inst.X.copy(), inst.ybar.copy(), {}
     if bad == "N1":
         X, y = X[:1], y[:1]
-    elif bad == "n33":
-        X = np.zeros((10, 33))
+    elif bad == "n_over":
+        X = np.zeros((10, crgb.CR_MAX_N + 1))
     elif bad == "gamma0":
         kw["gamma"] = 0.0
     elif bad == "nanX":

@@ -27,7 +27,8 @@ def _noalloc(X_dev, gamma, rule):
 
 def test_noalloc_matches_cr_create_on_two_calls_in_a_row():
     import torch
-    cases = [(3000, 20, 1e-4, crgb.CR_L_HESSIAN, "lse"), (777, 7, 1e-3, crgb.CR_L_PAPER, "maxaff")]
+    cases = [(3000, 20, 1e-4, crgb.CR_L_HESSIAN, "lse"), (777, 7, 1e-3, crgb.CR_L_PAPER, "maxaff"),
+             (900, 80, 1e-4, crgb.CR_L_HESSIAN, "exp"), (400, 128, 1e-4, crgb.CR_L_PAPER, "quad")]
     for N, n, gamma, rule, fam in cases:
         inst = cr_synth.make_instance(N, n, fam, 0.1, 5)
         with crgb.Solver(inst.X, inst.ybar, gamma=gamma, lipschitz_rule=rule) as s:
@@ -42,9 +43,10 @@ def test_noalloc_matches_cr_create_on_two_calls_in_a_row():
 def test_noalloc_rejects_what_its_scratch_cannot_hold():
     import torch
     lib = _capi.load()
-    Xd = torch.zeros((10, 33), dtype=torch.float64, device="cuda")
+    n_over = crgb.CR_MAX_N + 1
+    Xd = torch.zeros((10, n_over), dtype=torch.float64, device="cuda")
     L = ctypes.c_double()
-    assert lib.cr_lipschitz_noalloc(ctypes.c_void_p(Xd.data_ptr()), 10, 33, 1e-4, 0, None, ctypes.byref(L)) == 1
+    assert lib.cr_lipschitz_noalloc(ctypes.c_void_p(Xd.data_ptr()), 10, n_over, 1e-4, 0, None, ctypes.byref(L)) == 1
     assert b"scratch" in lib.cr_last_error()
     Xh = np.zeros((10, 3))
     assert lib.cr_lipschitz_noalloc(ctypes.c_void_p(Xh.ctypes.data), 10, 3, 1e-4, 0, None, ctypes.byref(L)) == 1
