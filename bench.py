@@ -301,8 +301,8 @@ def run_paper(args):
     torch.cuda.set_device(0)
     Ns = [200, 400] if args.paper_set == "small" else [200, 400, 800, 1600, 2400]
     rows = []
-    for fam in ("quad", "exp"):
-        for n in (20, 80):
+    for fam in (("exp",) if args.paper_set == "exp20" else ("quad", "exp")):
+        for n in ((20,) if args.paper_set == "exp20" else (20, 80)):
             for N in Ns:
                 inst = cr_synth.make_instance(N, n, fam, 10.0, 0, x_dist="normal4", interior_frac=0.3)
                 pname = args.precision if not (args.precision == "tf32" and n > crgb.CR_MAX_N_TF32) else "fp32"
@@ -330,16 +330,24 @@ def run_paper(args):
                                   "iterations": g["k"], "infeasibility": g["infeas_norm"],
                                   "dual_gap": abs(g["lagr_gap"]) / pairs, "primal_r": g["primal_r"],
                                   "dual_g": g["dual_g"]}
-                # p* of Eq. (regularize): a long adaptive restart run, bracketed by its certificate
-                with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, step_rule=crgb.CR_STEP_ADAPTIVE,
-                                 restart=1, check_every=200) as sv:
-                    _, gr = sv.solve(1e-7, args.max_sweeps * 4)
+                # p* of Eq. (regularize): a long adaptive restart run (FP64 where the working
+                # precision cannot resolve the gap: p* of the exp workloads is ~1e-2 of r at eta = 0)
+                ref_prec = "fp32"
+                with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=crgb.CR_FP32,
+                                 step_rule=crgb.CR_STEP_ADAPTIVE, restart=1, check_every=200) as sv:
+                    ok_r, gr = sv.solve(1e-7, args.max_sweeps * 4)
+                if not ok_r:
+                    ref_prec = "fp64"
+                    with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=crgb.CR_FP64,
+                                     step_rule=crgb.CR_STEP_ADAPTIVE, restart=1, check_every=500) as sv:
+                        ok_r, gr = sv.solve(1e-9, args.max_sweeps)
                 pstar = gr["dual_g"]
                 for r in runs.values():
                     r["subopt_reg"] = abs(r["primal_r"] - pstar) / abs(pstar)
                 line = {"config": {"f0": fam, "n": n, "N": N, "gamma": GAMMA, "precision": pname,
                                    "check_every": args.check_every, "max_sweeps": args.max_sweeps},
-                        "pstar": {"dual_g": pstar, "cert_primal": gr["cert_primal"], "rel_gap": gr["rel_gap"]},
+                        "pstar": {"dual_g": pstar, "cert_primal": gr["cert_primal"], "rel_gap": gr["rel_gap"],
+                                  "converged": bool(ok_r), "precision": ref_prec},
                         "runs": runs}
                 rows.append(line)
                 print(json.dumps(line), flush=True)
@@ -418,8 +426,8 @@ def main():
                     help="tf32: FP32 multipliers with hi+lo TF32 tensor-core contractions (the mixed-precision "
                          "configuration of the N = 20000 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paper-set", default="all", choices=["all", "small"],
-                    help="--mode paper: all of Section 5's N, or N in {200, 400}")
+    ap.add_argument("--paper-set", default="all", choices=["all", "small", "exp20"],
+                    help="--mode paper: all of Section 5's N, N in {200, 400}, or exp(p^T x) at n = 20 only")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "batch", "serve", "solve", "paper"],
                     help="sweep: lambda-pair rate of one instance; batch: solves/s of 256 instances; "
                          "serve: Poisson request stream through the serving runtime; solve: time to the "

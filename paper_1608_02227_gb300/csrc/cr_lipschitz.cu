@@ -13,6 +13,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "cr_host.h"
@@ -65,24 +67,31 @@ __global__ void scatter_kernel(const double *X, int N, int n, const double *mean
 
 // Jacobi eigendecomposition of the n x n symmetric Sc by one block of kJT threads, parallel
 // ordering: each sweep has m-1 rounds (m = n rounded up to even) of m/2 disjoint pairs (circle
-// schedule); thread i computes the rotation of pair i, then thread r applies all rotations of
-// the round to row/column r of A and to row r of V.  A lives in dynamic shared memory
-// (n^2 doubles), the rotations accumulate directly in V (n x n, columns = eigenvectors);
-// D (n) is written at the end.
-constexpr int kJT = CR_MAX_N;  // one thread per row, and at least m/2 threads
-static_assert(kJT % 32 == 0 && kJT >= 32, "whole warps");
+// schedule).  Thread i computes the rotation of pair i; then the n * m/2 (row, pair) updates
+// of A <- A J and V <- V J, and after them the (pair, column) updates of A <- J^T A, are spread
+// over the block.  The pairs of a round are disjoint, so every element receives exactly the
+// rotations of its own pair, in the same order, whichever thread applies them.  A lives in
+// dynamic shared memory (n^2 doubles) and so do the accumulated rotations when both fit
+// (n <= kJacobiVShared); above that they accumulate directly in V (n x n, columns =
+// eigenvectors).  D (n) and V are written at the end.
+constexpr int kJT = 512;
+static_assert(kJT % 32 == 0 && kJT >= CR_MAX_N, "whole warps, one thread per pair at least");
+constexpr int kJacobiVShared = 112;  // 2 n^2 doubles <= 200 KB of shared memory
+
+size_t jacobi_smem(int n) { return sizeof(double) * (size_t)n * n * (n <= kJacobiVShared ? 2 : 1); }
 
 __global__ void __launch_bounds__(kJT) jacobi_kernel(const double *Sc, int n, double *D, double *V) {
-    extern __shared__ double A[];  // n x n
+    extern __shared__ double A[];  // n x n, then (n <= kJacobiVShared) the rotations
     __shared__ double rc[CR_MAX_N / 2], rs[CR_MAX_N / 2];
     __shared__ int rp[CR_MAX_N / 2], rq[CR_MAX_N / 2];
     __shared__ double red[2][kJT / 32];
     __shared__ int done;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int m = (n + 1) & ~1;
+    const int m = (n + 1) & ~1, h = m / 2;
+    double *Q = n <= kJacobiVShared ? A + (size_t)n * n : V;
     for (int i = t; i < n * n; i += kJT) {
         A[i] = Sc[i];
-        V[i] = (i / n == i % n) ? 1.0 : 0.0;
+        Q[i] = (i / n == i % n) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
@@ -114,7 +123,7 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const double *Sc, int n, do
         __syncthreads();
         if (done) break;
         for (int round = 0; round < m - 1; ++round) {
-            if (t < m / 2) {
+            if (t < h) {
                 // circle method: position 0 fixed, the others rotate by `round`
                 const int a0 = t == 0 ? 0 : ((t - 1 + round) % (m - 1)) + 1;
                 const int b0 = ((m - 1 - t - 1 + round) % (m - 1)) + 1;
@@ -135,48 +144,52 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const double *Sc, int n, do
                 rs[t] = sn;
             }
             __syncthreads();
-            if (t < n) {  // A <- A J and V <- V J: row t, all pairs of the round
-                for (int i = 0; i < m / 2; ++i) {
-                    const int p = rp[i], q = rq[i];
-                    if (q >= n || rs[i] == 0.0) continue;
-                    const double c = rc[i], sn = rs[i];
-                    const double arp = A[t * n + p], arq = A[t * n + q];
-                    A[t * n + p] = c * arp - sn * arq;
-                    A[t * n + q] = sn * arp + c * arq;
-                    const double qrp = V[t * n + p], qrq = V[t * n + q];
-                    V[t * n + p] = c * qrp - sn * qrq;
-                    V[t * n + q] = sn * qrp + c * qrq;
-                }
+            for (int w = t; w < n * h; w += kJT) {  // A <- A J and V <- V J: (row r, pair i)
+                const int r = w / h, i = w - r * h;
+                const int p = rp[i], q = rq[i];
+                if (q >= n || rs[i] == 0.0) continue;
+                const double c = rc[i], sn = rs[i];
+                const double arp = A[r * n + p], arq = A[r * n + q];
+                A[r * n + p] = c * arp - sn * arq;
+                A[r * n + q] = sn * arp + c * arq;
+                const double qrp = Q[r * n + p], qrq = Q[r * n + q];
+                Q[r * n + p] = c * qrp - sn * qrq;
+                Q[r * n + q] = sn * qrp + c * qrq;
             }
             __syncthreads();
-            if (t < n) {  // A <- J^T A: column t, all pairs of the round
-                for (int i = 0; i < m / 2; ++i) {
-                    const int p = rp[i], q = rq[i];
-                    if (q >= n || rs[i] == 0.0) continue;
-                    const double c = rc[i], sn = rs[i];
-                    const double apr = A[p * n + t], aqr = A[q * n + t];
-                    A[p * n + t] = c * apr - sn * aqr;
-                    A[q * n + t] = sn * apr + c * aqr;
-                }
+            for (int w = t; w < n * h; w += kJT) {  // A <- J^T A: (pair i, column col)
+                const int i = w / n, col = w - i * n;
+                const int p = rp[i], q = rq[i];
+                if (q >= n || rs[i] == 0.0) continue;
+                const double c = rc[i], sn = rs[i];
+                const double apr = A[p * n + col], aqr = A[q * n + col];
+                A[p * n + col] = c * apr - sn * aqr;
+                A[q * n + col] = sn * apr + c * aqr;
             }
             __syncthreads();
         }
     }
     for (int i = t; i < n; i += kJT) D[i] = A[i * n + i];
+    if (Q != V)
+        for (int i = t; i < n * n; i += kJT) V[i] = Q[i];
 }
 
-__global__ void secular_kernel(const double *X, int N, int n, const double *mean, const double *D,
-                               const double *V, unsigned long long *best_bits) {
+// one thread per point; small blocks so that a few thousand points still spread over the SMs
+constexpr int kST = 64;
+
+__global__ void __launch_bounds__(kST) secular_kernel(const double *X, int N, int n, const double *mean,
+                                                      const double *D, const double *V,
+                                                      unsigned long long *best_bits) {
     extern __shared__ double sV[];  // n x n eigenvectors
     __shared__ double sD[CR_MAX_N];
     __shared__ double smean[CR_MAX_N];
-    for (int i = threadIdx.x; i < n * n; i += kT) sV[i] = V[i];
-    for (int i = threadIdx.x; i < n; i += kT) {
+    for (int i = threadIdx.x; i < n * n; i += kST) sV[i] = V[i];
+    for (int i = threadIdx.x; i < n; i += kST) {
         sD[i] = D[i];
         smean[i] = mean[i];
     }
     __syncthreads();
-    const int l = blockIdx.x * kT + threadIdx.x;
+    const int l = blockIdx.x * kST + threadIdx.x;
     double mu = 0.0;
     if (l < N) {
         double e[CR_MAX_N];
@@ -247,10 +260,10 @@ __global__ void secular_kernel(const double *X, int N, int n, const double *mean
         }
         mu = hi;
     }
-    __shared__ double sm[kT];
+    __shared__ double sm[kST];
     sm[threadIdx.x] = mu;
     __syncthreads();
-    for (int w = kT / 2; w > 0; w >>= 1) {
+    for (int w = kST / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
         __syncthreads();
     }
@@ -263,15 +276,16 @@ cudaError_t launch_eig_and_secular(const double *X, int N, int n, const double *
     static bool attr_set = false;  // per process; the attribute is per device function
     const int big = (int)(sizeof(double) * CR_MAX_N * CR_MAX_N);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        const int jbig = (int)std::max(jacobi_smem(kJacobiVShared), jacobi_smem(CR_MAX_N));
+        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, jbig);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const size_t sm = sizeof(double) * (size_t)n * n;
-    jacobi_kernel<<<1, kJT, sm, s>>>(Sc, n, D, V);
-    secular_kernel<<<(unsigned)((N + kT - 1) / kT), kT, sm, s>>>(X, N, n, mean, D, V, best);
+    jacobi_kernel<<<1, kJT, jacobi_smem(n), s>>>(Sc, n, D, V);
+    secular_kernel<<<(unsigned)((N + kST - 1) / kST), kST, sm, s>>>(X, N, n, mean, D, V, best);
     return cudaGetLastError();
 }
 
