@@ -157,7 +157,10 @@ cr_status rebuild(cr_batch *b) {
         while (npv[bi] != c->NP) ++bi;
         for (int rb = 0; rb < c->RB; ++rb)
             for (int sp = 0; sp < c->S; ++sp) per[bi].push_back(WorkItem{di, rb, sp});
-        work[bi] += (double)c->N * (double)c->ld;
+        // sweep cost of a pair grows with the padded width (FP32 TMA kernel, GB300: about
+        // (6 + NP) x 0.16 ps per pair from n = 8 to 32), so the concurrent buckets share the
+        // SMs by pairs x (6 + NP), not by pairs alone
+        work[bi] += (double)c->N * (double)c->ld * (6.0 + (double)c->NP);
         for (int blk = 0; blk < desc[di].fin_blocks; ++blk) fin.push_back(FinItem{di, blk});
     }
     // largest items first, so that the strided assignment of items to CTAs stays balanced
