@@ -39,6 +39,7 @@ import cr_synth  # noqa: E402
 METRIC = "lambda_pair_updates_per_s"
 UNIT = "pairs/s"
 GAMMA = 1e-4
+CPU_SAMPLE_S = 12.0           # host seconds of the oracle sample beside the GPU line
 L2_BYTES = 126 * 2**20        # GB300 L2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64
@@ -164,8 +165,10 @@ def cpu_baseline(workload):
     Ns = min(CPU_SAMPLE_N, inst.N)
     X, yb = inst.X[:Ns], inst.ybar[:Ns]
     o = oracle.PAPG(X, yb, GAMMA, oracle.lipschitz(X, GAMMA))
-    o.step(1, log=False)
-    iters = 6
+    t0 = time.perf_counter()
+    o.step(1, log=False)  # warm-up, also the calibration of the sample length
+    t1 = time.perf_counter() - t0
+    iters = int(min(500, max(3, round(CPU_SAMPLE_S / max(t1, 1e-3)))))  # about CPU_SAMPLE_S of host work
     t0 = time.perf_counter()
     o.step(iters, log=False)
     dt = time.perf_counter() - t0
