@@ -120,6 +120,34 @@ def _dist():
     return ws, rank, local
 
 
+def rank_instance(workload, rank, N=0):
+    """The instance a rank solves: the named workload drawn with seed + rank (replicas: each
+    rank holds its own independent instance of the same shape)."""
+    spec = dict(cr_synth.WORKLOADS[workload])
+    spec["seed"] = spec.get("seed", 0) + rank
+    if N:
+        spec["N"] = N
+    return cr_synth.make_instance(**spec)
+
+
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest value of x over all ranks (x itself when there is one rank)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(pairs_per_rank, steps, ws, t_max_ms):
+    """Whole-job rate: the pairs all ranks updated in `steps` iterations over the slowest
+    rank's time."""
+    return pairs_per_rank * steps * ws / (t_max_ms / 1e3)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -473,11 +501,7 @@ def main():
     else:
         torch.cuda.set_device(0)
     prec = {"fp32": crgb.CR_FP32, "fp64": crgb.CR_FP64, "tf32": crgb.CR_MIXED_TF32}[args.precision]
-    spec = dict(cr_synth.WORKLOADS[args.workload])
-    spec["seed"] = spec.get("seed", 0) + rank
-    if args.N:
-        spec["N"] = args.N
-    inst = cr_synth.make_instance(**spec)
+    inst = rank_instance(args.workload, rank, args.N)
     N, n = inst.N, inst.n
     pairs = N * (N - 1)
 
@@ -499,12 +523,8 @@ def main():
     clk = clocks.stop()
     gap = s.gap()
     s.close()
-    t_max = total_ms
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = pairs * args.steps * ws / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, ws)
+    value = job_rate(pairs, args.steps, ws, t_max)
 
     # end to end through the public API from host buffers
     barrier()
@@ -512,12 +532,8 @@ def main():
     with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec) as s2:
         s2.step(args.steps)
         y, xi = s2.primal()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": pairs * args.steps * ws / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": job_rate(pairs, args.steps, ws, 1e3 * e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": (inst.X.nbytes + inst.ybar.nbytes) / args.steps,
            "d2h_bytes_per_step": (y.nbytes + xi.nbytes) / args.steps}
 
