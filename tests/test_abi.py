@@ -65,6 +65,11 @@ def test_host_only_calls(lib):
     g = (ctypes.c_double * 1)(1e-3)
     assert lib.cr_solve_path(None, g, g, 1, 10, None) == 1
     assert lib.cr_solve_continuation(None, 0.1, 2.0, 0.1, 0.1, -1.0, 2, 10, None) == 1
+    # memory an instance of the batched work-list needs (host arithmetic only)
+    assert crgb.cr_batch_instance_bytes(1000, crgb.CR_MAX_N_BATCH + 1) == -1
+    assert crgb.cr_batch_instance_bytes(1, 4) == -1
+    b20, b40 = crgb.cr_batch_instance_bytes(1000, 20), crgb.cr_batch_instance_bytes(2000, 20)
+    assert b20 >= 2 * 1000 * 1000 * 4 and b40 > 3 * b20  # the two N x N FP32 buffers dominate
 
 
 def test_missing_library_fails_loudly(tmp_path):
