@@ -35,7 +35,7 @@ def _run_to_convergence(X, yb, gamma, iters):
 
 
 # --------------------------------------------------------------------------- operators
-@pytest.mark.parametrize("N,n,seed", [(5, 1, 0), (7, 3, 1), (9, 2, 2)])
+@pytest.mark.parametrize("N,n,seed", [(5, 1, 0), (7, 3, 1), (9, 2, 2), (5, 80, 3), (4, 128, 4)])
 def test_operators_match_definition1(N, n, seed):
     rng = np.random.default_rng(seed)
     X = rng.uniform(-1, 1, size=(N, n))
@@ -73,9 +73,8 @@ def test_lemma_o1_spectra(N):
     assert np.linalg.norm(A2, 2) <= Bx * N + 1e-12
 
 
-@pytest.mark.parametrize("gamma", [1e-1, 1e-3, 1e-4])
-def test_lipschitz_is_tight_upper_bound(gamma):
-    N, n = 9, 3
+@pytest.mark.parametrize("gamma,N,n", [(1e-1, 9, 3), (1e-3, 9, 3), (1e-4, 9, 3), (1e-4, 6, 80), (1e-3, 5, 128)])
+def test_lipschitz_is_tight_upper_bound(gamma, N, n):
     X = np.random.default_rng(4).uniform(-1, 1, size=(N, n))
     A1, A2 = qp_dense.dense_A(X)
     C = np.hstack([A1, A2])
