@@ -182,7 +182,8 @@ CR_API long long cr_iterations(const cr_ctx *ctx);
 /* Continuation in gamma (Section 6): changes gamma of Eq. (regularize) in place, keeping
  * lambda^k as the warm start theta^0 of the new problem.  Recomputes L by the context's rule from
  * the cached sigma_max(A2)^2 and the step (1/L, or upsilon/L for the adaptive rule), restarts the
- * momentum (t = 1, as Iteration 0 of Figure "papg") and rebuilds eta(lambda^k) for the new gamma.
+ * momentum (t = 1, as Iteration 0 of Figure "papg"), rebuilds eta(lambda^k) for the new gamma
+ * and recomputes the record's g, r and lambda^T C eta of lambda^k at the new gamma.
  * CR_EINVAL when gamma is not finite and > 0 or when the context was created with a caller-given
  * L (opt.lipschitz > 0), which cannot follow gamma. */
 CR_API cr_status cr_set_gamma(cr_ctx *ctx, double gamma);

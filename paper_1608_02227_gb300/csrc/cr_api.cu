@@ -961,6 +961,25 @@ CR_API cr_status cr_set_gamma(cr_ctx *c, double gamma) {
     h.s = c->adaptive ? c->opt.upsilon / c->L : 1.0 / c->L;
     h.prev_g = -DBL_MAX;
     h.accepted = 1;
+    // g, r and lambda^T C eta of lambda^k at the new gamma (the record held the old gamma's):
+    // the finalize's sums of (a, b)^k, in FP64 on the host
+    {
+        const size_t nb = (size_t)N * c->n;
+        std::vector<double> av((size_t)N), bv(nb), yv((size_t)N);
+        CR_CUDA(cudaMemcpyAsync(av.data(), c->ha[h.k & 1], sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+        CR_CUDA(cudaMemcpyAsync(bv.data(), c->hb[h.k & 1], sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+        CR_CUDA(cudaMemcpyAsync(yv.data(), c->ybar, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+        CR_CUDA(cudaStreamSynchronize(c->stream));
+        double aa = 0.0, ay = 0.0, bb = 0.0;
+        for (int l = 0; l < N; ++l) {
+            aa += av[l] * av[l];
+            ay += av[l] * yv[l];
+        }
+        for (size_t q = 0; q < nb; ++q) bb += bv[q] * bv[q];
+        h.last_g = -0.5 * aa - ay - bb / (2.0 * gamma);
+        h.last_r = 0.5 * aa + bb / (2.0 * gamma);
+        h.last_lg = aa + ay + bb / gamma;
+    }
     CR_CUDA(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     return rebuild_recovery(c, h);
 }

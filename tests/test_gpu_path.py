@@ -68,10 +68,17 @@ def test_restore_rejects_another_shape():
 def test_continuation_stage_is_a_warm_start_fp64():
     inst = cr_synth.make_instance(150, 3, "sqnorm", 0.1, 34)
     g0, g1 = 1e-2, 1e-3
+    o_mid = oracle.PAPG(inst.X, inst.ybar, g0, oracle.lipschitz(inst.X, g0))
+    o_mid.step(60, log=False)
+    d_mid = oracle.dual_obj(inst.X, inst.ybar, g1, o_mid.theta)  # theta^60 under the new gamma
     with crgb.Solver(inst.X, inst.ybar, gamma=g0, precision=crgb.CR_FP64) as s:
         s.step(60)
         s.set_gamma(g1)
         assert abs(s.L - oracle.lipschitz(inst.X, g1)) <= 1e-12 * s.L
+        # the record describes lambda^k at the new gamma (the stop tests of a stage compare it)
+        gm = s.gap()
+        assert abs(gm["dual_g"] - d_mid["g"]) <= 1e-10 * abs(d_mid["g"])
+        assert abs(gm["primal_r"] - d_mid["r"]) <= 1e-10 * abs(d_mid["r"])
         s.step(60)
         y, xi = s.primal()
         lam = s.lam()
