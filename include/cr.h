@@ -215,7 +215,8 @@ CR_API cr_status cr_solve_continuation(cr_ctx *ctx, double eps0, double beta, do
  * vectors of eta the next sweep reads and the device scalars, as one block of
  * cr_checkpoint_bytes(ctx) bytes in caller-owned memory (host or device).  cr_restore loads a
  * block into a context created for the same instance and options (CR_EINVAL when its shape,
- * precision or step rule differ); the next iterations are bitwise those of the saved run. */
+ * precision or step rule differ, or when X or ybar differ: the block carries a fingerprint
+ * of both); the next iterations are bitwise those of the saved run. */
 CR_API long long cr_checkpoint_bytes(const cr_ctx *ctx);
 CR_API cr_status cr_checkpoint(cr_ctx *ctx, void *buf, long long bytes);
 CR_API cr_status cr_restore(cr_ctx *ctx, const void *buf, long long bytes);

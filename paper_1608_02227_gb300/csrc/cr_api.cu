@@ -935,7 +935,31 @@ struct CkptHeader {
     char magic[8];
     long long N, ld, k, nbuf, tsz;
     int n, precision, step_rule, pad;
+    unsigned long long data_fp;  // FNV-1a of the instance's X and ybar bytes
 };
+constexpr char kCkptMagic[9] = "CRCKPT02";
+
+// FNV-1a (64-bit) over the bytes of X and ybar as the context holds them: a checkpoint is
+// restored only into a context created for the same data.
+cr_status data_fingerprint(cr_ctx *c, unsigned long long *fp) {
+    const size_t nx = (size_t)c->N * c->n;
+    std::vector<double> hx(nx), hy((size_t)c->N);
+    CR_CUDA(cudaMemcpyAsync(hx.data(), c->X, sizeof(double) * nx, cudaMemcpyDeviceToHost, c->stream));
+    CR_CUDA(cudaMemcpyAsync(hy.data(), c->ybar, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    CR_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long h = 1469598103934665603ull;
+    auto eat = [&h](const std::vector<double> &v) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(v.data());
+        for (size_t i = 0, e = v.size() * sizeof(double); i < e; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    eat(hx);
+    eat(hy);
+    *fp = h;
+    return CR_OK;
+}
 
 }  // namespace crh
 
@@ -1054,7 +1078,8 @@ CR_API cr_status cr_checkpoint(cr_ctx *c, void *buf, long long bytes) {
         return CR_EINVAL;
     }
     CkptHeader hd{};
-    memcpy(hd.magic, "CRCKPT01", 8);
+    memcpy(hd.magic, kCkptMagic, 8);
+    CR_TRY(data_fingerprint(c, &hd.data_fp));
     hd.N = c->N;
     hd.ld = c->ld;
     hd.k = c->k;
@@ -1093,10 +1118,16 @@ CR_API cr_status cr_restore(cr_ctx *c, const void *buf, long long bytes) {
     const char *p = (const char *)buf;
     CR_CUDA(cudaMemcpy(&hd, p, sizeof(hd), cudaMemcpyDefault));
     p += sizeof(hd);
-    if (memcmp(hd.magic, "CRCKPT01", 8) != 0 || hd.N != c->N || hd.n != c->n || hd.ld != c->ld ||
+    if (memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.N != c->N || hd.n != c->n || hd.ld != c->ld ||
         hd.precision != c->opt.precision || hd.step_rule != c->opt.step_rule ||
         hd.nbuf != (c->adaptive ? 3 : 2) || hd.tsz != (is_f64(c) ? 8 : 4)) {
         set_err("the checkpoint belongs to another instance shape, precision or step rule");
+        return CR_EINVAL;
+    }
+    unsigned long long fp = 0;
+    CR_TRY(data_fingerprint(c, &fp));
+    if (fp != hd.data_fp) {
+        set_err("the checkpoint was taken on other data (X or ybar differ)");
         return CR_EINVAL;
     }
     DevState h{};

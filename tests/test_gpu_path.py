@@ -63,6 +63,15 @@ def test_restore_rejects_another_shape():
     with crgb.Solver(a_inst.X, a_inst.ybar, precision=crgb.CR_FP32, **ADAPT) as c:
         with pytest.raises(crgb.CRError):
             c.restore(buf)
+    # same shape and options, other data
+    other = cr_synth.make_instance(300, 4, "sqnorm", 0.1, 99)
+    with crgb.Solver(other.X, other.ybar, precision=crgb.CR_FP32) as d:
+        with pytest.raises(crgb.CRError):
+            d.restore(buf)
+    # and the block restores into a fresh context on the same data
+    with crgb.Solver(a_inst.X, a_inst.ybar, precision=crgb.CR_FP32) as e:
+        e.restore(buf)
+        assert e.k == 3
 
 
 def test_continuation_stage_is_a_warm_start_fp64():
