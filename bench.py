@@ -290,8 +290,6 @@ def run_solve(args):
     runs = {}
     for name, rule, restart in (("adaptive_restart", crgb.CR_STEP_ADAPTIVE, 1), ("adaptive", crgb.CR_STEP_ADAPTIVE, 0),
                                 ("constant", crgb.CR_STEP_CONSTANT, 0)):
-        if rule == crgb.CR_STEP_ADAPTIVE and prec == crgb.CR_FP32:
-            continue
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, step_rule=rule, restart=restart,
