@@ -24,7 +24,7 @@ def test_two_gloo_ranks_share_the_bench_bookkeeping(tmp_path):
     out = tmp_path / "ranks.json"
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "tests", "multirank_worker.py"), str(out)]
+           os.path.join(ROOT, "tests", "multirank_child.py"), str(out)]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=240)
     assert r.returncode == 0, r.stderr[-2000:]
