@@ -164,13 +164,16 @@ CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
  * memory at the moment they need L -- e.g. an admission controller that budgets HBM before
  * reserving it, a framework whose caching allocator owns all of HBM, or a latency-critical
  * loop where cudaMalloc/cudaFree would synchronise the device).
- *   X: N x n points, FP64, row-major, DEVICE memory only (host pointers are rejected with
- *   CR_EINVAL); rule: CR_L_HESSIAN or CR_L_PAPER; stream: cudaStream_t or NULL; *L receives
- *   the same value cr_create computes for these inputs.  Synchronises the stream.
+ *   X: N x n points, FP64, row-major, DEVICE memory of the current device only (host
+ *   pointers and memory of another device are rejected with CR_EINVAL); rule: CR_L_HESSIAN or
+ *   CR_L_PAPER; stream: cudaStream_t or NULL; *L receives the same value cr_create computes
+ *   for these inputs.  Errors as cr_create: CR_EINVAL for bad sizes or a non-finite entry of
+ *   X, CR_ENUMERIC when L comes out non-finite or <= 0, CR_ECUDA for a failed CUDA call.
  * Limit: 1 <= n <= CR_MAX_N (128); the scratch is a fixed 264 KB array in device memory that
  * every GPU which loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating call is made.  The first call on a device (with that device current)
- * looks up the array's device address; make that first call before any stream capture.
+ * looks up the array's device address.  Every call copies the result to the host and
+ * synchronises the stream, so it cannot be made while that stream is being captured.
  * Every call shares the array: calls whose work overlaps on the GPU (two streams or threads
  * at once) race and must be serialised by the caller. */
 CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, int n, double gamma, int rule, void *stream,
@@ -226,18 +229,22 @@ CR_API void cr_destroy(cr_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------
  * Batched solving: many independent instances (uneven N and n) iterate together.  Every
- * iteration is one persistent TMA sweep launch per point-dimension bucket over a device
- * work-list of (instance, 32-row block, column split) items -- the buckets run as parallel
- * branches of a captured CUDA graph -- followed by one finalize launch over all instances.
+ * iteration is one persistent sweep launch per bucket over a device work-list of (instance,
+ * row block, column split) items -- one bucket per padded point dimension for the FP32 TMA
+ * sweep (32-row blocks), one bucket for all tensor-core instances (128-row blocks); the
+ * buckets run as parallel branches of a captured CUDA graph -- followed by one finalize
+ * launch over all instances.
  * Each instance keeps its own multipliers, step constant, t_k and iteration count, and is
  * retired at its own convergence check (the K = N method of Figure "papg" per instance).
  * A batch is bound to one stream and is not thread-safe.
  * ------------------------------------------------------------------------------------ */
 typedef struct cr_batch cr_batch;
 
-/* opt: NULL for the defaults (precision must be CR_FP32; graph_iters is the number of
- * iterations per captured graph; check_every the iterations between checks in
- * cr_batch_run).  stream: as in cr_create. */
+/* opt: NULL for the defaults (precision CR_FP32 or CR_MIXED_TF32; graph_iters is the number
+ * of iterations per captured graph; check_every the iterations between checks in
+ * cr_batch_run).  With CR_MIXED_TF32 every instance with n <= CR_MAX_N_TF32 runs the
+ * tensor-core sweep (all of them in one persistent launch over a work-list of 128-row items)
+ * and an n = 32 instance runs the FP32 sweep.  stream: as in cr_create. */
 CR_API cr_status cr_batch_create(const cr_options *opt, void *stream, cr_batch **out);
 
 /* Adds one instance (X: N x n with n <= CR_MAX_N_BATCH, ybar: N; host or device; copied).  It is retired once a
@@ -263,8 +270,9 @@ CR_API cr_status cr_batch_primal(cr_batch *b, int id, double *y, double *xi);
 /* Releases the device memory of instance id (active or retired); the id stays invalid. */
 CR_API cr_status cr_batch_remove(cr_batch *b, int id);
 
-/* Device bytes that an instance of N points in n dimensions takes in a batch with the constant
- * step (the adaptive step adds a third multiplier buffer, 4 N ceil32(N) bytes, and O(N n)). */
+/* Device bytes that an instance of N points in n dimensions takes at most in a batch with the
+ * constant step, in either precision (the adaptive step adds a third multiplier buffer,
+ * 4 N ceil32(N) bytes, and O(N n)). */
 CR_API long long cr_batch_instance_bytes(long long N, int n);
 
 /* Times `iters` iterations of the active instances for each column-split width in

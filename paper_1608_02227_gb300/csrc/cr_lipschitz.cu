@@ -270,18 +270,30 @@ __global__ void __launch_bounds__(kST) secular_kernel(const double *X, int N, in
     if (threadIdx.x == 0) atomicMax(best_bits, (unsigned long long)__double_as_longlong(sm[0]));
 }
 
+constexpr int kAttrDevices = 128;
+
 // The two kernels with n^2 doubles of dynamic shared memory (up to 128 KB at n = 128).
 cudaError_t launch_eig_and_secular(const double *X, int N, int n, const double *mean, const double *Sc, double *D,
                                    double *V, unsigned long long *best, cudaStream_t s) {
-    static bool attr_set = false;  // per process; the attribute is per device function
+    // the large dynamic shared-memory attribute applies to the current device only: set it
+    // once per device, under a lock (callers on several threads or devices share this)
+    static std::mutex mu;
+    static bool attr_set[kAttrDevices] = {};
     const int big = (int)(sizeof(double) * CR_MAX_N * CR_MAX_N);
-    if (!attr_set) {
-        const int jbig = (int)std::max(jacobi_smem(kJacobiVShared), jacobi_smem(CR_MAX_N));
-        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, jbig);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr_set[dev]) {
+            const int jbig = (int)std::max(jacobi_smem(kJacobiVShared), jacobi_smem(CR_MAX_N));
+            e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, jbig);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
     }
     const size_t sm = sizeof(double) * (size_t)n * n;
     jacobi_kernel<<<1, kJT, jacobi_smem(n), s>>>(Sc, n, D, V);
@@ -328,8 +340,9 @@ cudaError_t a2_sigma_sq(const double *X, int N, int n, double *out_host, cudaStr
 // ------------------------------------------------------------------------------------
 namespace {
 
-// mean (n) + scatter (n^2) + eigenvectors (n^2) + eigenvalues (n) + one 64-bit max word,
-// for n <= CR_MAX_N: 2 * 128 * 128 + 2 * 128 + 8 doubles = 264 KB.
+// mean (n) + scatter (n^2) + eigenvectors (n^2) + eigenvalues (n), then (in the last two
+// words) the non-finite flag of X and the 64-bit max word, for n <= CR_MAX_N:
+// 2 * 128 * 128 + 2 * 128 + 8 doubles = 264 KB.
 constexpr int kLipScratchDoubles = 2 * CR_MAX_N * CR_MAX_N + 2 * CR_MAX_N + 8;
 static __device__ __align__(256) double g_lip_scratch[kLipScratchDoubles];
 
@@ -358,6 +371,12 @@ extern "C" CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, i
         set_err("gamma must be finite and > 0, rule CR_L_HESSIAN or CR_L_PAPER");
         return CR_EINVAL;
     }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_err("cudaGetDevice failed or device %d out of range: %s", dev, cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, X) != cudaSuccess ||
         (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
@@ -365,11 +384,9 @@ extern "C" CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, i
         set_err("X must be device memory (the allocation-free path cannot stage host data)");
         return CR_EINVAL;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        set_err("cudaGetDevice failed or device %d out of range: %s", dev, cudaGetErrorString(e));
-        return CR_ECUDA;
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+        set_err("X lives on device %d but device %d is current: make X's device current first", at.device, dev);
+        return CR_EINVAL;
     }
     double *scr = nullptr;
     {
@@ -388,23 +405,38 @@ extern "C" CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, i
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *mean = scr, *Sc = mean + n, *V = Sc + (size_t)n * n, *D = V + (size_t)n * n;
-    unsigned long long *best = reinterpret_cast<unsigned long long *>(scr + kLipScratchDoubles - 1);
-    // the max word is the only scratch read before it is written: clear it every call
-    e = cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
+    // the last two words: the non-finite flag of X and the max word; they are the only
+    // scratch read before it is written, so both are cleared on every call
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(scr + kLipScratchDoubles - 2);
+    int *finite_flag = reinterpret_cast<int *>(words);
+    unsigned long long *best = words + 1;
+    e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cr::launch_check_finite(X, N * (long long)n, finite_flag, s);
     if (e == cudaSuccess) {
         mean_kernel<<<n, kT, 0, s>>>(X, (int)N, n, mean);
         scatter_kernel<<<n * (n + 1) / 2, kT, 0, s>>>(X, (int)N, n, mean, Sc);
         e = cr::launch_eig_and_secular(X, (int)N, n, mean, Sc, D, V, best, s);
     }
-    unsigned long long bits = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, best, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    unsigned long long hw[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hw, words, sizeof(hw), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_err("cr_lipschitz_noalloc failed: %s", cudaGetErrorString(e));
         return CR_ECUDA;
     }
+    int nonfinite = 0;
+    memcpy(&nonfinite, &hw[0], sizeof(nonfinite));
+    if (nonfinite) {
+        set_err("X contains a non-finite value");
+        return CR_EINVAL;
+    }
     double s2;
-    memcpy(&s2, &bits, sizeof(s2));
-    *L = (rule == CR_L_PAPER) ? (2.0 * (double)N + s2) / gamma : 2.0 * (double)N + s2 / gamma;
+    memcpy(&s2, &hw[1], sizeof(s2));
+    const double Lv = (rule == CR_L_PAPER) ? (2.0 * (double)N + s2) / gamma : 2.0 * (double)N + s2 / gamma;
+    if (!(Lv > 0.0) || !isfinite(Lv)) {
+        set_err("non-finite or non-positive step constant L = %g", Lv);
+        return CR_ENUMERIC;
+    }
+    *L = Lv;
     return CR_OK;
 }
