@@ -186,6 +186,90 @@ def run_reference(args):
     return 0
 
 
+def solve_record(crgb, inst, prec, tol=1e-4, max_sweeps=20000):
+    """The solve half of the metric on the timed instance: cr_solve to rel_gap <= tol with the
+    adaptive step of Section 4 and momentum restart, through the public API from host buffers
+    (creation, the step constant and the copies included)."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, step_rule=crgb.CR_STEP_ADAPTIVE,
+                     restart=1, upsilon=2.0, check_every=100) as s:
+        t1 = time.perf_counter()
+        ok, g = s.solve(tol, max_sweeps)
+        y, xi = s.primal()
+    t2 = time.perf_counter()
+    return {"converged": bool(ok), "tol": tol, "wall_s": t2 - t0, "create_s": t1 - t0, "sweeps": g["sweeps"],
+            "iterations": g["k"], "rel_gap": g["rel_gap"], "dual_g": g["dual_g"], "solves_per_s": 1.0 / (t2 - t0),
+            "rule": "adaptive + restart", "max_sweeps": max_sweeps}
+
+
+def batch_record(crgb, count=64, tol=1e-4, max_iter=20000):
+    """Batched solves against the plain single-instance path on the same instances: `count`
+    instances of the batched workload (N log-uniform in [100, 4000], n in {2..16},
+    ||x||^2 + N(0, 0.1^2)), mixed precision, adaptive step + restart, each to rel_gap <= tol.
+    Completion times count from the moment all instances are handed over (t = 0)."""
+    import torch
+
+    insts = cr_synth.batch_workload(count, seed=0)
+    ropt = dict(step_rule=crgb.CR_STEP_ADAPTIVE, upsilon=2.0, restart=1)
+    check = 100
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_at = {}
+    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check, precision=crgb.CR_MIXED_TF32, **ropt) as b:
+        ids = [b.add(i.X, i.ybar, tol=tol, max_iter=max_iter) for i in insts]
+        active = len(ids)
+        while active:
+            active = b.step(check)
+            now = time.perf_counter() - t0
+            for i in ids:
+                if i not in done_at and b.poll(i)[0]:
+                    done_at[i] = now
+        conv = sum(1 for i in ids if b.poll(i)[1] == 0)
+    wall = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    plain_at, plain_conv = [], 0
+    for inst in insts:
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20,
+                         precision=_prec(crgb, "tf32", inst.n), **ropt) as s:
+            ok, _ = s.solve(tol, max_iter)
+        plain_conv += int(ok)
+        plain_at.append(time.perf_counter() - t1)
+    plain_wall = time.perf_counter() - t1
+    lat = list(done_at.values())
+    return {"workload": f"batch{count}_sqnorm_N100-4000_n2-16", "precision": "tf32", "tol": tol,
+            "batched": {"solves_per_s": count / wall, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99),
+                        "converged": conv, "wall_s": wall},
+            "plain_single_instance": {"solves_per_s": count / plain_wall, "p50_s": pct(plain_at, 0.5),
+                                      "p99_s": pct(plain_at, 0.99), "converged": plain_conv, "wall_s": plain_wall}}
+
+
+def cpu_one_core(workload, seconds=6.0):
+    """The oracle on one host core (OMP_NUM_THREADS=1 in a fresh process): pairs/s."""
+    code = ("import json, time, sys; sys.path.insert(0, %r); import cr_synth, oracle; "
+            "inst = cr_synth.workload(%r); Ns = 2000; X, yb = inst.X[:Ns], inst.ybar[:Ns]; "
+            "o = oracle.PAPG(X, yb, %r, oracle.lipschitz(X, %r)); t0 = time.perf_counter(); o.step(1, log=False); "
+            "t1 = time.perf_counter() - t0; it = int(max(2, min(200, %r / max(t1, 1e-3)))); "
+            "t0 = time.perf_counter(); o.step(it, log=False); dt = time.perf_counter() - t0; "
+            "print(json.dumps({'value': Ns * (Ns - 1) * it / dt, 'cores': oracle.threads(), "
+            "'sample': 'first %%d points, %%d iterations (%%.1f s)' %% (Ns, it, dt)}))"
+            % (ROOT, workload, GAMMA, GAMMA, seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1:] or ["failed"]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["unit"] = UNIT
+    return d
+
+
 def cpu_baseline(workload):
     import oracle
 
@@ -202,6 +286,14 @@ def cpu_baseline(workload):
     dt = time.perf_counter() - t0
     return {"value": Ns * (Ns - 1) * iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"first {Ns} points of {workload}, {iters} FP64 oracle iterations ({dt:.1f} s)"}
+
+
+def _prec(crgb, name, n=None):
+    """Library precision for a --precision name; n = 32 points run the FP32 sweep under tf32
+    (the tensor-core operand carries a row of ones, so it holds n <= 31), as batches do."""
+    if name == "tf32" and n is not None and n > crgb.CR_MAX_N_TF32:
+        name = "fp32"
+    return {"fp32": crgb.CR_FP32, "fp64": crgb.CR_FP64, "tf32": crgb.CR_MIXED_TF32}[name]
 
 
 def _rule_options(crgb, rule):
@@ -229,7 +321,8 @@ def run_batch(args):
     t0 = time.perf_counter()
     done_at = {}
     pairs = 0.0
-    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check, **ropt) as b:
+    with crgb.Batch(gamma=GAMMA, graph_iters=20, check_every=check, precision=_prec(crgb, args.precision),
+                    **ropt) as b:
         ids = [b.add(i.X, i.ybar, tol=args.tol, max_iter=max_iter) for i in insts]
         t_setup = time.perf_counter() - t0
         width = b.autotune(2)
@@ -250,7 +343,8 @@ def run_batch(args):
     t1 = time.perf_counter()
     plain_done, plain_conv = 0, 0
     for inst in insts:
-        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20, **ropt) as s:
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20,
+                         precision=_prec(crgb, args.precision, inst.n), **ropt) as s:
             ok, _ = s.solve(args.tol, max_iter)
         plain_done += 1
         plain_conv += int(ok)
@@ -261,7 +355,8 @@ def run_batch(args):
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch{len(insts)}_sqnorm_N100-4000_n2-16", "gamma": GAMMA, "tol": args.tol,
-                       "check_every": check, "tile_cols": width, "step_rule": args.rule},
+                       "check_every": check, "tile_cols": width, "step_rule": args.rule,
+                       "precision": args.precision},
             "converged": conv, "lambda_pairs_per_s": pairs / wall, "setup_s": t_setup, "wall_s": wall,
             "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                           "max": lat[-1]},
@@ -400,7 +495,7 @@ def run_serve(args):
     t0 = time.perf_counter()
     ropt = _rule_options(crgb, args.rule)
     with crgb.Server(mem_cap_bytes=60 << 30, max_active=256, gamma=GAMMA, check_every=check,
-                     graph_iters=20, **ropt) as srv:
+                     graph_iters=20, precision=_prec(crgb, args.precision), **ropt) as srv:
         ids = []
         for t_arr, inst in reqs:
             delay = t_arr - (time.perf_counter() - t0)
@@ -422,7 +517,8 @@ def run_serve(args):
     for t_arr, inst in reqs:
         start = max(clock, t_arr)
         s0 = time.perf_counter()
-        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20, **ropt) as s:
+        with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, check_every=check, graph_iters=20,
+                         precision=_prec(crgb, args.precision, inst.n), **ropt) as s:
             ok, rec = s.solve(args.tol, max_iter)
         clock = start + (time.perf_counter() - s0)
         lat_plain.append(clock - t_arr)
@@ -436,7 +532,7 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serve_poisson{args.rate:g}_{len(reqs)}req_N200-{args.N_max}_n2-32",
                        "gamma": GAMMA, "tol": args.tol, "max_iter": max_iter, "mem_cap_GB": 60,
-                       "step_rule": args.rule},
+                       "step_rule": args.rule, "precision": args.precision},
             "served": served, "plain_single_instance": plain,
             "offered_rate": args.rate, "achieved_rate": served["solves_per_s"]}
     print(json.dumps(line), flush=True)
@@ -472,6 +568,9 @@ def main():
     ap.add_argument("--N-max", type=int, default=4000, help="largest N of a request in --mode serve")
     ap.add_argument("--count", type=int, default=256, help="instances in --mode batch")
     ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--quick", action="store_true",
+                    help="default mode: skip the solve and batch records (profiling runs)")
+    ap.add_argument("--batch-count", type=int, default=64, help="instances of the batch record")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -513,12 +612,13 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # clock samples cover the whole measured block (the timed sweeps, the end-to-end run and
+    # the solve and batch records): the timed region alone can be shorter than one sample
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     sweep_ms, total_ms = crgb.cr_dual_step_timed(s.ctx, args.steps)
     barrier()
-    clk = clocks.stop()
     gap = s.gap()
     s.close()
     t_max = max_over_ranks(total_ms, ws)
@@ -534,6 +634,11 @@ def main():
     e2e = {"value": job_rate(pairs, args.steps, ws, 1e3 * e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": (inst.X.nbytes + inst.ybar.nbytes) / args.steps,
            "d2h_bytes_per_step": (y.nbytes + xi.nbytes) / args.steps}
+    extras = {}
+    if not args.quick and ws == 1:
+        extras["solve"] = solve_record(crgb, inst, prec, tol=args.tol)
+        extras["batch"] = batch_record(crgb, count=args.batch_count, tol=args.tol)
+    clk = clocks.stop()
 
     if rank == 0:
         peak, src = _peaks()
@@ -584,8 +689,10 @@ def main():
             "clocks": clk,
             "gap_at_end": {"k": gap["k"], "rel_gap": gap["rel_gap"], "dual_g": gap["dual_g"]},
         }
+        line.update(extras)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload)
+            line["cpu_baseline"]["one_core"] = cpu_one_core(args.workload)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -403,8 +403,10 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         }
         CR_TRY(dev_alloc(c, &c->tc_ld, 3));
         CR_TRY(dev_alloc(c, &c->tc_st, 3));
-        CR_CUDA(cudaMemcpyAsync(c->tc_ld, hl, sizeof(hl), cudaMemcpyHostToDevice, c->stream));
-        CR_CUDA(cudaMemcpyAsync(c->tc_st, hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
+        memcpy(c->tc_lam_ld, hl, sizeof(hl));
+        memcpy(c->tc_lam_st, hs, sizeof(hs));
+        CR_CUDA(cudaMemcpyAsync(c->tc_ld, c->tc_lam_ld, sizeof(hl), cudaMemcpyHostToDevice, c->stream));
+        CR_CUDA(cudaMemcpyAsync(c->tc_st, c->tc_lam_st, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
         CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));

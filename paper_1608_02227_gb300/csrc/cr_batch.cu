@@ -24,7 +24,7 @@ using namespace crh;
 
 namespace {
 
-constexpr int kMaxBuckets = 12;
+constexpr int kMaxBuckets = 13;  // twelve FP32 widths and the tensor-core sweep
 constexpr int kMinSplit = 512;  // smallest column-split width (sizes the row partials)
 constexpr int kDefaultSplit = 4096;
 
@@ -38,9 +38,11 @@ struct BatchInst {
     cr_gap_info info{};
 };
 
+// np > 0: the FP32 TMA sweep of that padded width; np == kTcBucket: the tensor-core sweep
 struct Bucket {
     int np, off, count, grid;
 };
+constexpr int kTcBucket = 0;
 
 }  // namespace
 
@@ -133,6 +135,19 @@ void fill_desc(const cr_batch *b, const cr_ctx *c, InstDesc *d, int id) {
     d->xT32 = c->xT32;
     d->finblk = c->finblk;
     d->log = c->log;
+    d->tc = c->tc ? 1 : 0;
+    d->dgroups = c->S * (c->tc ? 2 : 1);  // the tensor-core sweep keeps two groups per split
+    if (c->tc) {
+        for (int i = 0; i < 3; ++i) {
+            d->tc_lam_ld[i] = c->tc_lam_ld[i];
+            d->tc_lam_st[i] = c->tc_lam_st[i];
+        }
+        d->tc_xrh = c->tcm.XRh;
+        d->tc_xrl = c->tcm.XRl;
+        d->tc_xt = c->tcm.XT;
+        d->tc_y = c->tcm.Y;
+        d->xi_rm = c->xi_rm;
+    }
     (void)b;
 }
 
@@ -147,20 +162,22 @@ cr_status rebuild(cr_batch *b) {
     std::vector<std::vector<WorkItem>> per(kMaxBuckets);
     std::vector<double> work(kMaxBuckets, 0.0);
     std::vector<FinItem> fin;
-    static const int npv[kMaxBuckets] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+    static const int npv[kMaxBuckets] = {kTcBucket, 2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
     for (int di = 0; di < na; ++di) {
         cr_ctx *c = b->inst[b->active[di]].c;
         c->cps = std::max(kMinSplit, (int)std::min<long long>(b->cps, round_up(c->ld, kChunk)));
         c->S = (int)((c->ld + c->cps - 1) / c->cps);
         fill_desc(b, c, &desc[di], b->active[di]);
         int bi = 0;
-        while (npv[bi] != c->NP) ++bi;
+        if (!c->tc)
+            while (npv[bi] != c->NP) ++bi;
         for (int rb = 0; rb < c->RB; ++rb)
             for (int sp = 0; sp < c->S; ++sp) per[bi].push_back(WorkItem{di, rb, sp});
-        // sweep cost of a pair grows with the padded width (FP32 TMA kernel, GB300: about
-        // (6 + NP) x 0.16 ps per pair from n = 8 to 32), so the concurrent buckets share the
-        // SMs by pairs x (6 + NP), not by pairs alone
-        work[bi] += (double)c->N * (double)c->ld * (6.0 + (double)c->NP);
+        // sweep cost of a pair grows with the padded width in the FP32 TMA kernel (GB300: about
+        // (6 + NP) x 0.16 ps per pair from n = 8 to 32), and is about 2.2 ps (~14 of those units)
+        // for any n in the tensor-core kernel, so the concurrent buckets share the SMs by
+        // pairs x cost, not by pairs alone
+        work[bi] += (double)c->N * (double)c->ld * (c->tc ? 14.0 : 6.0 + (double)c->NP);
         for (int blk = 0; blk < desc[di].fin_blocks; ++blk) fin.push_back(FinItem{di, blk});
     }
     // largest items first, so that the strided assignment of items to CTAs stays balanced
@@ -182,7 +199,10 @@ cr_status rebuild(cr_batch *b) {
         bk.off = (int)items.size();
         bk.count = (int)v.size();
         int occ = 1;
-        sweep_tma_occupancy(bk.np, &occ);
+        if (bk.np == kTcBucket)
+            sweep_tc_occupancy(&occ);
+        else
+            sweep_tma_occupancy(bk.np, &occ);
         const double share = total > 0 ? work[bi] / total : 1.0;
         bk.grid = (int)std::max(1.0, std::round(share * b->sms * std::max(1, occ)));
         bk.grid = std::min(bk.grid, bk.count);
@@ -210,8 +230,11 @@ cr_status enqueue_batch_iteration(cr_batch *b) {
     for (size_t i = 0; i < b->buckets.size(); ++i) {
         const Bucket &bk = b->buckets[i];
         CR_CUDA(cudaStreamWaitEvent(b->aux[i], b->ev_fork, 0));
-        CR_CUDA(launch_sweep_tma_batch(bk.np, b->d_desc, b->d_items + bk.off, bk.count, b->d_err, bk.grid,
-                                       b->opt.step_rule == CR_STEP_ADAPTIVE, b->aux[i]));
+        if (bk.np == kTcBucket)
+            CR_CUDA(launch_sweep_tc_batch(b->d_desc, b->d_items + bk.off, bk.count, b->d_err, bk.grid, b->aux[i]));
+        else
+            CR_CUDA(launch_sweep_tma_batch(bk.np, b->d_desc, b->d_items + bk.off, bk.count, b->d_err, bk.grid,
+                                           b->opt.step_rule == CR_STEP_ADAPTIVE, b->aux[i]));
         CR_CUDA(cudaEventRecord(b->ev_join[i], b->aux[i]));
         CR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
     }
@@ -335,8 +358,8 @@ CR_API cr_status cr_batch_create(const cr_options *opt, void *stream, cr_batch *
         o = *opt;
     else
         cr_default_options(&o);
-    if (o.precision != CR_FP32) {
-        set_err("batches run the FP32 sweep (precision must be CR_FP32)");
+    if (o.precision != CR_FP32 && o.precision != CR_MIXED_TF32) {
+        set_err("batches run the FP32 or the mixed-precision sweep (precision CR_FP32 or CR_MIXED_TF32)");
         return CR_EINVAL;
     }
     if (o.graph_iters < 0 || (o.graph_iters & 1)) {
@@ -393,11 +416,14 @@ CR_API cr_status cr_batch_add(cr_batch *b, const double *X, const double *ybar, 
     cr_options o = b->opt;
     o.tile_cols = kMinSplit;  // row partials sized for the narrowest split the batch may use
     o.graph_iters = 0;
+    // the tensor-core sweep carries a row of ones in its 32-wide operand (n <= 31): a
+    // mixed-precision batch runs an n = 32 instance on the FP32 sweep
+    if (o.precision == CR_MIXED_TF32 && n > CR_MAX_N_TF32) o.precision = CR_FP32;
     cr_ctx *c = nullptr;
     CR_TRY(cr_create(X, ybar, N, n, &o, b->stream, &c));
-    if (!c->tma) {
+    if (!c->tma && !c->tc) {
         cr_destroy(c);
-        set_err("batches need the TMA sweep");
+        set_err("batches need the TMA or the tensor-core sweep");
         return CR_EUNSUPPORTED;
     }
     BatchInst bi;
@@ -470,6 +496,7 @@ CR_API long long cr_batch_instance_bytes(long long N, int n) {
     b += 3 * NP * ldv * 4 + 8 * ldv * 4;          // points, xi (sweep, certificate), y/u splits
     b += 8 * N * n + 8 * N + 4 * 8 * N * (n + 1); // X, ybar, C^T history
     b += 8 * (N + N * n) + 16 * R * N + 8 * gN * 5 + 8 * 3 * 4096 + 4096;
+    if (n <= CR_MAX_N_TF32) b += 3 * 2 * ldv * 32 * 4 + 6 * 128 + 4096;  // tensor-core operands and maps
     return b;
 }
 

@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDes
     a.ul = D.ul;
     a.xiT = D.xiT;
     a.xT32 = D.xT32;
+    a.xi_rm = D.xi_rm;
     a.blockpart = D.finblk;
     a.log = D.log;
     a.st = D.st;
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDes
             a.hist_b[i] = D.hb[i];
         }
         a.dpart = D.dpart;
-        a.dgroups = D.col_splits;
+        a.dgroups = D.dgroups;
         finalize_adapt_body<float>(a, it.block, D.fin_blocks);
     } else {
         finalize_body<float>(a, it.block, D.fin_blocks);
@@ -498,6 +499,7 @@ __global__ void commit_batch_kernel(const InstDesc *d, const FinItem *items) {
     a.ul = D.ul;
     a.xiT = D.xiT;
     a.xT32 = D.xT32;
+    a.xi_rm = D.xi_rm;
     a.st = D.st;
     commit_point(a, it.block * kFX + (int)threadIdx.x);
 }

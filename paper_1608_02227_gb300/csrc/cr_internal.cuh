@@ -208,6 +208,13 @@ struct WorkItem {
 struct InstDesc {
     CUtensorMap tm_lam[3];               // lam[0..2]: [N][ld], box 128 x R (the third with the adaptive step)
     CUtensorMap tm_x, tm_y, tm_xi, tm_u; // as in TmaMaps
+    // tensor-core instances (tc = 1): load (box 32 x 128) and store (box 32 x 32) maps of the
+    // multiplier buffers and the point / y maps of TcMaps
+    CUtensorMap tc_lam_ld[3], tc_lam_st[3];
+    CUtensorMap tc_xrh, tc_xrl, tc_xt, tc_y;
+    int tc;
+    int dgroups;                         // adaptive step: groups of the row sums in dpart
+    float *xi_rm;                        // tensor-core instances: xi rows [2][ldv][32]
     float *lam[3];
     int adaptive;
     float *dpart;                        // adaptive step: [S][N] row sums of (lambda^k - lambda~^k)^2
@@ -225,6 +232,10 @@ struct InstDesc {
 };
 cudaError_t launch_sweep_tma_batch(int np, const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
                                    bool adaptive, cudaStream_t s);
+// the tensor-core sweep over a work-list of (instance, 128-row block, column split) items of
+// tensor-core instances (any n <= CR_MAX_N_TF32 in one launch)
+cudaError_t launch_sweep_tc_batch(const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
+                                  cudaStream_t s);
 struct FinItem {
     int inst, block;
 };

@@ -34,6 +34,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <mutex>
+
 #include "cr_internal.cuh"
 
 namespace cr {
@@ -70,6 +72,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 128u;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
+constexpr int kTcDevices = 128;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -240,21 +243,94 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
 }
 __device__ __forceinline__ float tf32_lo(float v) { return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
-struct Item {
-    int rb, sp, i0;
-    long long c0, c1;
-    int nch;
+// Everything one work item of 128 rows x one column split needs: the tensor maps of its
+// instance, its vectors and partial buffers, the roles of its multiplier buffers and its bounds.
+struct TcView {
+    const CUtensorMap *P, *Q, *Qs;           // lambda^{k-1}, lambda^{k-2} loads; store map of lambda^k
+    const CUtensorMap *XRh, *XRl, *XT, *Y;   // point rows (hi, lo), transposed points, y (hi, lo)
+    const float *xi_rm, *u;
+    float *rowpart, *colpart, *dpart;
+    const DevState *st;
+    long long ld, ldv, c0, c1;
+    int N, n, NP, rb, sp, i0, nch, adaptive;
 };
-__device__ __forceinline__ Item item_of(const TcSweepArgs &a, int item) {
-    Item it;
-    it.rb = item / a.col_splits;
-    it.sp = item - it.rb * a.col_splits;
-    it.i0 = it.rb * kM;
-    it.c0 = (long long)it.sp * a.cols_per_split;
-    it.c1 = min(it.c0 + (long long)a.cols_per_split, a.ld);
-    it.nch = (int)((it.c1 - it.c0 + kC - 1) / kC);
-    return it;
+
+__device__ __forceinline__ void tc_bounds(TcView &v, int cols_per_split) {
+    v.i0 = v.rb * kM;
+    v.c0 = (long long)v.sp * cols_per_split;
+    v.c1 = min(v.c0 + (long long)cols_per_split, v.ld);
+    v.nch = (int)((v.c1 - v.c0 + kC - 1) / kC);
 }
+
+// One instance: the point maps are kernel parameters; items tile [0, N) x [0, ld).
+struct TcSrcSingle {
+    const CUtensorMap *XRh, *XRl, *XT, *Y;
+    const TcSweepArgs *a;
+    __device__ __forceinline__ int count() const { return a->row_blocks * a->col_splits; }
+    __device__ __forceinline__ TcView view(int item) const {
+        TcView v;
+        int bp, bq, br;
+        lam_roles(a->st, a->adaptive, a->p_host, &bp, &bq, &br);
+        v.P = a->lmaps + bp;
+        v.Q = a->lmaps + bq;
+        v.Qs = a->smaps + br;
+        v.XRh = XRh, v.XRl = XRl, v.XT = XT, v.Y = Y;
+        v.xi_rm = a->xi_rm;
+        v.u = a->u;
+        v.rowpart = a->rowpart;
+        v.colpart = a->colpart;
+        v.dpart = a->dpart;
+        v.st = a->st;
+        v.ld = a->ld;
+        v.ldv = a->ldv;
+        v.N = a->N;
+        v.n = a->n;
+        v.NP = a->NP;
+        v.adaptive = a->adaptive;
+        v.rb = item / a->col_splits;
+        v.sp = item - v.rb * a->col_splits;
+        tc_bounds(v, a->cols_per_split);
+        return v;
+    }
+};
+
+// Many instances: per-instance descriptors (tensor maps included) in global memory and a
+// work-list of (instance, 128-row block, column split).  The roles of each instance's
+// multiplier buffers follow from its own device state (iteration parity, or the ring of
+// the adaptive step), so a captured graph replays correctly for instances that joined late.
+struct TcSrcBatch {
+    const InstDesc *d;
+    const WorkItem *w;
+    int n;
+    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ TcView view(int item) const {
+        const WorkItem wi = w[item];
+        const InstDesc &D = d[wi.inst];
+        TcView v;
+        int bp, bq, br;
+        lam_roles(D.st, D.adaptive, (int)(D.st->k & 1), &bp, &bq, &br);
+        v.P = &D.tc_lam_ld[bp];
+        v.Q = &D.tc_lam_ld[bq];
+        v.Qs = &D.tc_lam_st[br];
+        v.XRh = &D.tc_xrh, v.XRl = &D.tc_xrl, v.XT = &D.tc_xt, v.Y = &D.tc_y;
+        v.xi_rm = D.xi_rm;
+        v.u = D.uh;
+        v.rowpart = D.rowpart;
+        v.colpart = D.colpart;
+        v.dpart = D.dpart;
+        v.st = D.st;
+        v.ld = D.ld;
+        v.ldv = D.ldv;
+        v.N = D.N;
+        v.n = D.n;
+        v.NP = D.NP;
+        v.adaptive = D.adaptive;
+        v.rb = wi.rb;
+        v.sp = wi.sp;
+        tc_bounds(v, D.cols_per_split);
+        return v;
+    }
+};
 
 // Steps 4 and 2 for one thread's 32 entries of a chunk row: lambda~ = P + beta (P - Q),
 // lambda = max(0, lambda~ + s rho), rho = (u_h - y_h) + (u_l - y_l) + S; the new lambda
@@ -309,10 +385,8 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    sweep_tc_kernel(const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
-                    const __grid_constant__ CUtensorMap tmXT, const __grid_constant__ CUtensorMap tmY,
-                    const TcSweepArgs a) {
+template <class Src>
+__device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -338,11 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int items = a.row_blocks * a.col_splits;
-    // buffer roles: lambda^{k-1} and lambda^{k-2} are loaded, the output is stored by warps
-    int bp, bq, br;
-    lam_roles(a.st, a.adaptive, a.p_host, &bp, &bq, &br);
-    const CUtensorMap *tmP = a.lmaps + bp, *tmQ = a.lmaps + bq, *tmQs = a.smaps + br;
+    const int items = src.count();
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -389,20 +459,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t fill = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-                const Item it = item_of(a, item);
+                const TcView it = src.view(item);
                 for (int c = 0; c < it.nch; ++c, ++fill) {
                     const int s = fill % kStages;
                     const int j0 = (int)(it.c0 + (long long)c * kC);
-                    if (!slot_wait(&empty[s], fill / kStages, abort_flag, a.err)) {
+                    if (!slot_wait(&empty[s], fill / kStages, abort_flag, err)) {
                         ok = false;
                         break;
                     }
                     unsigned char *st = stage0 + (size_t)s * kStageBytes;
                     bar_expect(&full[s], kTxStage);
-                    tma_load(st + kOffP, tmP, &full[s], j0, it.i0);
-                    tma_load(st + kOffQ, tmQ, &full[s], j0, it.i0);
-                    tma_load(st + kOffXT, &tmXT, &full[s], j0, 0);
-                    tma_load(y0 + (size_t)s * kYBytes, &tmY, &full[s], j0, 0);
+                    tma_load(st + kOffP, it.P, &full[s], j0, it.i0);
+                    tma_load(st + kOffQ, it.Q, &full[s], j0, it.i0);
+                    tma_load(st + kOffXT, it.XT, &full[s], j0, 0);
+                    tma_load(y0 + (size_t)s * kYBytes, it.Y, &full[s], j0, 0);
                 }
             }
             // drain the copies still in flight before the CTA can exit
@@ -418,18 +488,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t pf = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-                const Item it = item_of(a, item);
+                const TcView it = src.view(item);
                 for (int pc = 0; 2 * pc < it.nch; ++pc, ++pf) {
                     const int x = pf % kXr;
                     const int j0 = (int)(it.c0 + (long long)pc * 2 * kC);
-                    if (!slot_wait(&rempty[x], pf / kXr, abort_flag, a.err)) {
+                    if (!slot_wait(&rempty[x], pf / kXr, abort_flag, err)) {
                         ok = false;
                         break;
                     }
                     unsigned char *xr = xr0 + (size_t)x * kXrBytes;
                     bar_expect(&rfull[x], kXrBytes);
-                    tma_load(xr, &tmXRh, &rfull[x], 0, j0);
-                    tma_load(xr + kXrHalf, &tmXRl, &rfull[x], 0, j0);
+                    tma_load(xr, it.XRh, &rfull[x], 0, j0);
+                    tma_load(xr + kXrHalf, it.XRl, &rfull[x], 0, j0);
                 }
             }
             for (uint32_t f = pf > (uint32_t)kXr ? pf - kXr : 0; f < pf; ++f) {
@@ -448,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g1_pair = 0, g1_itn = 0;
             auto g1_norm = [&](void) -> bool {  // advance to a valid (item, pair); false at the end
                 while (g1_item < items) {
-                    if (2 * g1_pc < item_of(a, g1_item).nch) return true;
+                    if (2 * g1_pc < src.view(g1_item).nch) return true;
                     g1_item += gridDim.x;
                     g1_pc = 0;
                     ++g1_itn;
@@ -462,23 +532,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 return g1_pair < (uint32_t)kSBufs || bar_test(&sempty[b], (g1_pair / kSBufs - 1) & 1u);
             };
             auto issue_gemm1 = [&](void) -> bool {
-                const Item it = item_of(a, g1_item);
+                const int it_nch = src.view(g1_item).nch;
                 const int x = g1_pair % kXr, b = g1_pair % kSBufs, xb = g1_itn & 1;
-                if (!bar_wait(&rfull[x], g1_pair / kXr, abort_flag, a.err)) return false;
-                if (g1_pc == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, a.err)) return false;
-                if (!slot_wait(&sempty[b], g1_pair / kSBufs, abort_flag, a.err)) return false;
+                if (!bar_wait(&rfull[x], g1_pair / kXr, abort_flag, err)) return false;
+                if (g1_pc == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, err)) return false;
+                if (!slot_wait(&sempty[b], g1_pair / kSBufs, abort_flag, err)) return false;
                 tc_fence_after();
                 const uint32_t xr = su32(xr0 + (size_t)x * kXrBytes);
                 gemm1(tS(b), tX(xb), xr, xr + kXrHalf);
                 mma_commit(&sfull[b]);
                 mma_commit(&rempty[x]);
-                if (2 * (g1_pc + 1) >= it.nch) mma_commit(&xempty[xb]);
+                if (2 * (g1_pc + 1) >= it_nch) mma_commit(&xempty[xb]);
                 ++g1_pc;
                 ++g1_pair;
                 return true;
             };
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
-                const Item it = item_of(a, item);
+                const TcView it = src.view(item);
                 const int ab = itn & 1;
                 for (int c = 0; c < it.nch && ok; ++c, ++fill) {
                     if (c > 0 && (c & 1) == 0) ++cur_pair;
@@ -490,12 +560,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (!ok) break;
                     const int s = fill % kStages;
-                    if (!bar_wait(&full[s], fill / kStages, abort_flag, a.err) ||
-                        !bar_wait(&lamr[s], fill / kStages, abort_flag, a.err)) {
+                    if (!bar_wait(&full[s], fill / kStages, abort_flag, err) ||
+                        !bar_wait(&lamr[s], fill / kStages, abort_flag, err)) {
                         ok = false;
                         break;
                     }
-                    if (c == 0 && !slot_wait(&aempty[ab], itn >> 1, abort_flag, a.err)) {
+                    if (c == 0 && !slot_wait(&aempty[ab], itn >> 1, abort_flag, err)) {
                         ok = false;
                         break;
                     }
@@ -518,17 +588,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int h = (warp - 2) >> 2;          // group: takes the chunks of parity h in an item
         const int r = 32 * q + lane;            // row within the item
         const uint32_t lq = (uint32_t)(32 * q) << 16;
-        const float2 beta2 = make_float2((float)a.st->beta, (float)a.st->beta);
-        const float2 s2 = make_float2((float)a.st->s, (float)a.st->s);
         // the first group copies the xi rows (hi, lo) of an item into tensor-memory buffer
         // xitn & 1, once the GEMM1s of the item that used that buffer before are done
         auto put_xi = [&](int item, uint32_t xitn) -> bool {
             const int xb = xitn & 1;
-            const bool ok = __all_sync(0xffffffffu, slot_wait(&xempty[xb], xitn >> 1, abort_flag, a.err));
+            const bool ok = __all_sync(0xffffffffu, slot_wait(&xempty[xb], xitn >> 1, abort_flag, err));
             if (ok) {
-                const long long row = (long long)item_of(a, item).i0 + r;  // < ldv
-                const float4 *hi = reinterpret_cast<const float4 *>(a.xi_rm + row * 32);
-                const float4 *lo = reinterpret_cast<const float4 *>(a.xi_rm + a.ldv * 32 + row * 32);
+                const TcView xv = src.view(item);
+                const long long row = (long long)xv.i0 + r;  // < ldv
+                const float4 *hi = reinterpret_cast<const float4 *>(xv.xi_rm + row * 32);
+                const float4 *lo = reinterpret_cast<const float4 *>(xv.xi_rm + xv.ldv * 32 + row * 32);
                 float v[32];
                 tc_fence_after();
 #pragma unroll
@@ -554,14 +623,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         if (h == 0 && blockIdx.x < items) ok = put_xi(blockIdx.x, 0);
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
-            const Item it = item_of(a, item);
+            const TcView it = src.view(item);
             const int ab = itn & 1;
             const int i = it.i0 + r;
-            const bool rv = i < a.N;
+            const bool rv = i < it.N;
+            const float2 beta2 = make_float2((float)it.st->beta, (float)it.st->beta);
+            const float2 s2 = make_float2((float)it.st->s, (float)it.st->s);
             // xi rows of the next item go into the other tensor-memory buffer now, so that
             // GEMM1 can run ahead across the item boundary
             if (h == 0 && item + (int)gridDim.x < items) ok = put_xi(item + gridDim.x, itn + 1) && ok;
-            const float uh = a.u[i], ul = a.u[a.ldv + i];  // i < ldv
+            const float uh = it.u[i], ul = it.u[it.ldv + i];  // i < ldv
             const float2 uh2 = make_float2(uh, uh), ul2 = make_float2(ul, ul);
             float dsum = 0.f;  // this thread's part of the row's ||lambda^k - lambda~^k||^2
             for (int c = 0; c < it.nch; ++c, ++fill) {
@@ -570,8 +641,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int s = fill % kStages, b = pair % kSBufs;
                 const long long j0 = it.c0 + (long long)c * kC;
                 unsigned char *st = stage0 + (size_t)s * kStageBytes;
-                ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, a.err);
-                ok = ok && bar_wait(&sfull[b], pair / kSBufs, abort_flag, a.err);
+                ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, err);
+                ok = ok && bar_wait(&sfull[b], pair / kSBufs, abort_flag, err);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
                 float v[kC];
                 tc_fence_after();
@@ -584,24 +655,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
                     float *Qs = reinterpret_cast<float *>(st + kOffQ);
-                    const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > a.N) ||
-                                      (it.i0 + kM > a.N);
-                    if (a.adaptive) {
+                    const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N) ||
+                                      (it.i0 + kM > it.N);
+                    if (it.adaptive) {
                         if (edge)
-                            epi_chunk<true, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                            epi_chunk<true, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
                         else
-                            epi_chunk<false, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                            epi_chunk<false, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
                     } else if (edge) {
-                        epi_chunk<true, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                        epi_chunk<true, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
                     } else {
-                        epi_chunk<false, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, a.N, dsum);
+                        epi_chunk<false, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
                     }
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
                 }
                 __syncwarp();
                 if (lane == 0) {
                     // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
-                    if (ok && it.i0 + 32 * q < a.N) tma_store(tmQs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
+                    if (ok && it.i0 + 32 * q < it.N) tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
                     bar_arrive(&lamr[s]);
                 }
                 if (ok) {
@@ -644,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float *colx = reinterpret_cast<const float *>(colx0 + (size_t)s * kColxBytes);
                         const float cv = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
                         const long long j = j0 + lane;
-                        if (j < it.c1) a.colpart[(long long)it.rb * a.ld + j] = cv;
+                        if (j < it.c1) it.colpart[(long long)it.rb * it.ld + j] = cv;
                     }
                     __syncwarp();
                     if (lane == 0) ticket[s] = 0;
@@ -658,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // end of item: row partials from the GEMM2 accumulator: columns k < n of the two
             // halves give sum_j lambda_ij x_jk, column n of the first gives sum_j lambda_ij;
             // this group reads columns [16 h, 16 h + 16) of both halves
-            const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, a.err));
+            const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, err));
             float acc[kHalf], acl[kHalf];
             tc_fence_after();
             if (ok2) {
@@ -668,14 +739,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&aempty[ab]);
-            if (a.adaptive && ok && rv) a.dpart[((long long)it.sp * 2 + h) * a.N + i] = dsum;
+            if (it.adaptive && ok && rv) it.dpart[((long long)it.sp * 2 + h) * it.N + i] = dsum;
             if (ok2 && rv) {
-                float *dst = a.rowpart + ((long long)it.sp * a.N + i) * (a.NP + 1);
+                float *dst = it.rowpart + ((long long)it.sp * it.N + i) * (it.NP + 1);
 #pragma unroll
                 for (int e = 0; e < kHalf; ++e) {
                     const int k = kHalf * h + e;
-                    if (k < a.n) dst[k] = acc[e] + acl[e];
-                    if (k == a.n) dst[a.NP] = acc[e];
+                    if (k < it.n) dst[k] = acc[e] + acl[e];
+                    if (k == it.n) dst[it.NP] = acc[e];
                 }
             }
             ok = ok && ok2;
@@ -689,17 +760,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+__global__ void __launch_bounds__(kThreads, 1)
+    sweep_tc_kernel(const __grid_constant__ CUtensorMap tmXRh, const __grid_constant__ CUtensorMap tmXRl,
+                    const __grid_constant__ CUtensorMap tmXT, const __grid_constant__ CUtensorMap tmY,
+                    const TcSweepArgs a) {
+    const TcSrcSingle src{&tmXRh, &tmXRl, &tmXT, &tmY, &a};
+    sweep_tc_body(src, a.err);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sweep_tc_batch_kernel(const InstDesc *d, const WorkItem *w, int nitems, int *err) {
+    const TcSrcBatch src{d, w, nitems};
+    sweep_tc_body(src, err);
+}
+
 }  // namespace
 
 size_t sweep_tc_smem() { return kSmem; }
 int sweep_tc_rows() { return kM; }
 
 cudaError_t sweep_tc_occupancy(int *blocks_per_sm) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    // the large shared-memory attribute is per device: set it once on each, under a lock
+    static std::mutex mu;
+    static bool attr[kTcDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kTcDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr[dev]) {
+            e = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+            if (e != cudaSuccess) return e;
+            attr[dev] = true;
+        }
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep_tc_kernel, kThreads, kSmem);
 }
@@ -709,6 +803,27 @@ cudaError_t launch_sweep_tc(const TcMaps &m, const TcSweepArgs &a, int grid, cud
     cudaError_t e = sweep_tc_occupancy(&occ);
     if (e != cudaSuccess) return e;
     sweep_tc_kernel<<<grid, kThreads, kSmem, s>>>(m.XRh, m.XRl, m.XT, m.Y, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_tc_batch(const InstDesc *d, const WorkItem *w, int nitems, int *err, int grid,
+                                  cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static bool attr[kTcDevices] = {};
+    if (dev < 0 || dev >= kTcDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr[dev]) {
+            e = cudaFuncSetAttribute(sweep_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+            if (e != cudaSuccess) return e;
+            attr[dev] = true;
+        }
+    }
+    sweep_tc_batch_kernel<<<grid, kThreads, kSmem, s>>>(d, w, nitems, err);
     return cudaGetLastError();
 }
 

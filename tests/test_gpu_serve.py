@@ -77,3 +77,56 @@ def test_oversized_request_is_refused():
         with pytest.raises(crgb.CRError) as e:
             srv.submit(inst.X, inst.ybar)
         assert e.value.status == 2
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_tf32_served_results_equal_alone():
+    # mixed precision: tensor-core instances (n <= 31) and an n = 32 instance on the FP32
+    # sweep share the server's launches; each equals its single-instance run bitwise
+    insts = _stream(6, seed=4, N_lo=300, N_hi=1400, n_lo=2, n_hi=31)
+    insts.append(cr_synth.make_instance(500, 32, "lse", 0.1, 1099))
+    gamma = 1e-3
+    with crgb.Server(tile_cols=512, mem_cap_bytes=8 << 30, max_active=64, gamma=gamma, check_every=25,
+                     graph_iters=4, precision=crgb.CR_MIXED_TF32) as srv:
+        ids = []
+        for inst in insts:
+            ids.append(srv.submit(inst.X, inst.ybar, tol=1e-4, max_iter=2000))
+            time.sleep(0.02)
+        for r in ids:
+            srv.wait(r, 300)
+        res = [(srv.poll(r), srv.result(r)) for r in ids]
+    for inst, ((state, status, info, lat), (y, xi)) in zip(insts, res):
+        assert state == 2 and status in (0, 4)
+        prec = crgb.CR_MIXED_TF32 if inst.n <= crgb.CR_MAX_N_TF32 else crgb.CR_FP32
+        with crgb.Solver(inst.X, inst.ybar, gamma=gamma, tile_cols=512, graph_iters=0, precision=prec) as s:
+            s.step(int(info["k"]))
+            ys, xis = s.primal()
+        assert np.array_equal(y, ys) and np.array_equal(xi, xis), (inst.N, inst.n)
+
+
+@pytest.mark.parametrize("precision", [crgb.CR_FP32, crgb.CR_MIXED_TF32])
+def test_served_results_match_oracle(precision):
+    # every request of a small mixed stream against the FP64 oracle run for the same number
+    # of iterations (Figure "papg", constant step), at the reduced-precision tolerances:
+    # 1e-4 on y, 1e-3 on xi (relative 2-norms and element by element), 1e-4 on g
+    import oracle
+    insts = _stream(5, seed=7, N_lo=120, N_hi=420, n_lo=2, n_hi=14)
+    gamma = 1e-3
+    with crgb.Server(tile_cols=512, mem_cap_bytes=4 << 30, max_active=16, gamma=gamma, check_every=50,
+                     graph_iters=4, precision=precision) as srv:
+        ids = [srv.submit(i.X, i.ybar, tol=1e-4, max_iter=1500) for i in insts]
+        for r in ids:
+            srv.wait(r, 300)
+        res = [(srv.poll(r), srv.result(r)) for r in ids]
+    for inst, ((state, status, info, lat), (y, xi)) in zip(insts, res):
+        assert state == 2 and status in (0, 4), (status, info)
+        L = oracle.lipschitz(inst.X, gamma)
+        o = oracle.PAPG(inst.X, inst.ybar, gamma, L)
+        log = o.step(int(info["k"]))
+        yr, xir = o.primal()
+        assert _rel(y, yr) <= 1e-4 and np.abs(y - yr).max() <= 1e-4 * np.abs(yr).max(), (inst.N, inst.n)
+        assert _rel(xi, xir) <= 1e-3 and np.abs(xi - xir).max() <= 1e-3 * np.abs(xir).max(), (inst.N, inst.n)
+        assert abs(info["dual_g"] - log["g"][-1]) <= 1e-4 * abs(log["g"][-1])
