@@ -571,6 +571,9 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="default mode: skip the solve and batch records (profiling runs)")
     ap.add_argument("--batch-count", type=int, default=64, help="instances of the batch record")
+    ap.add_argument("--refresh", type=int, default=64,
+                    help="iterations between exact FP64 re-evaluations of C^T lambda (0: C^T from FP32 partials "
+                         "every iteration, no delta form)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -602,7 +605,7 @@ def main():
     N, n = inst.N, inst.n
     pairs = N * (N - 1)
 
-    s = crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec)
+    s = crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, refresh_every=args.refresh)
     desc = s.describe()
     s.step(args.warmup)
     torch.cuda.synchronize()
@@ -627,7 +630,7 @@ def main():
     # end to end through the public API from host buffers
     barrier()
     t0 = time.perf_counter()
-    with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec) as s2:
+    with crgb.Solver(inst.X, inst.ybar, gamma=GAMMA, precision=prec, refresh_every=args.refresh) as s2:
         s2.step(args.steps)
         y, xi = s2.primal()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
@@ -682,10 +685,12 @@ def main():
                        "l2": l2_note,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "grid": desc["grid"], "rows_per_item": desc["rows_per_item"],
-                       "col_splits": desc["col_splits"]},
+                       "col_splits": desc["col_splits"], "ct_delta_form": bool(desc.get("delta")),
+                       "refresh_every": desc.get("refresh_every", 0)},
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            # per iteration: sweep + finalize (+ the three gated kernels of the exact C^T refresh)
+            "gpu_launches": (2 + (3 if desc.get("delta") else 0)) * args.steps,
             "clocks": clk,
             "gap_at_end": {"k": gap["k"], "rel_gap": gap["rel_gap"], "dual_g": gap["dual_g"]},
         }

@@ -92,6 +92,11 @@ typedef struct cr_options {
     double upsilon;      /* CR_STEP_ADAPTIVE: the factor upsilon > 1 of the step rule (default 2) */
     int restart;         /* 1: reset the momentum (t = 1) when g_gamma(lambda^k) < g_gamma(lambda^{k-1}),
                             function-value restart of the accelerated iteration (not in the paper) */
+    int refresh_every;   /* CR_FP32 / CR_MIXED_TF32 with n <= 32: > 0 reduces each sweep's change of the
+                            multipliers, (a,b)^k = (a,b)^{k-1} + C^T (lambda^k - lambda^{k-1}) in FP64, and
+                            re-evaluates C^T lambda^k exactly in FP64 from the stored multipliers every
+                            refresh_every iterations; 0 forms C^T lambda^k from FP32 partials every
+                            iteration (default 64) */
 } cr_options;
 
 /* Convergence record for eta(lambda^k), the primal of Theorem "rate". */
@@ -110,7 +115,7 @@ typedef struct cr_gap_info {
 
 /* Fills *opt with the defaults: gamma 1e-4, lipschitz 0 (computed), CR_L_HESSIAN,
  * CR_FP32, accelerate 1, check_every 100, graph_iters 32, tile_cols 0, CR_STEP_CONSTANT,
- * upsilon 2. */
+ * upsilon 2, restart 0, refresh_every 64. */
 CR_API void cr_default_options(cr_options *opt);
 
 /* Creates a solver for one instance (Eq. (regularize)).
@@ -178,6 +183,15 @@ CR_API cr_status cr_lipschitz(const cr_ctx *ctx, double *L);
  * at once) race and must be serialised by the caller. */
 CR_API cr_status cr_lipschitz_noalloc(const double *X, long long N, int n, double gamma, int rule, void *stream,
                                       double *L);
+
+/* Failure-path hook (the paper has no counterpart): bounds every wait of the FP32 TMA sweep's
+ * consumer warps for data to land (default 2 s) by consumer_wait_ns nanoseconds (0 restores
+ * the default).  The producer's waits keep their normal bound, so every copy it issued lands
+ * before a CTA exits.  A wait that runs out makes the sweep abort cleanly; the next cr_gap or
+ * cr_solve on the context returns CR_ETIMEOUT and the context's iterate is no longer valid
+ * (destroy it; other contexts are unaffected).  For tests of the timeout path; CR_EUNSUPPORTED
+ * when the context does not run the TMA sweep. */
+CR_API cr_status cr_set_wait_limit(cr_ctx *ctx, long long consumer_wait_ns);
 
 /* Iterations taken so far (sweeps with CR_STEP_ADAPTIVE). */
 CR_API long long cr_iterations(const cr_ctx *ctx);

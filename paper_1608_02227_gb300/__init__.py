@@ -12,13 +12,15 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import (CR_FP32, CR_FP64, CR_L_HESSIAN, CR_L_PAPER, CR_MAX_N, CR_MAX_N_BATCH, CR_MAX_N_TF32,
-                    CR_MIXED_TF32, CR_STEP_ADAPTIVE, CR_STEP_CONSTANT, CRError,
+from ._capi import (CR_ECUDA, CR_EINVAL, CR_ENOMEM, CR_ENOTCONV, CR_ENUMERIC, CR_ETIMEOUT, CR_EUNSUPPORTED,
+                    CR_FP32, CR_FP64, CR_L_HESSIAN, CR_L_PAPER, CR_MAX_N, CR_MAX_N_BATCH, CR_MAX_N_TF32,
+                    CR_MIXED_TF32, CR_OK, CR_STEP_ADAPTIVE, CR_STEP_CONSTANT, CRError,
                     cr_gap_info, cr_options, check)
 
 __all__ = [
     "CR_FP64", "CR_FP32", "CR_MIXED_TF32", "CR_L_HESSIAN", "CR_L_PAPER", "CR_MAX_N", "CR_MAX_N_TF32",
-    "CR_MAX_N_BATCH", "CRError",
+    "CR_MAX_N_BATCH", "CRError", "CR_OK", "CR_EINVAL", "CR_ENOMEM", "CR_ECUDA", "CR_ENOTCONV", "CR_ETIMEOUT",
+    "CR_ENUMERIC", "CR_EUNSUPPORTED",
     "CR_STEP_CONSTANT", "CR_STEP_ADAPTIVE",
     "default_options", "cr_create", "cr_dual_step", "cr_dual_step_timed", "cr_solve", "cr_primal",
     "cr_gap", "cr_lambda", "cr_lipschitz", "cr_iterations", "cr_describe", "cr_destroy", "Solver",

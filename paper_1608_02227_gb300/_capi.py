@@ -35,6 +35,7 @@ class cr_options(ctypes.Structure):
         ("step_rule", ctypes.c_int),
         ("upsilon", ctypes.c_double),
         ("restart", ctypes.c_int),
+        ("refresh_every", ctypes.c_int),
     ]
 
 
@@ -101,6 +102,7 @@ _SIGS = [
     ("cr_lipschitz_noalloc", ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp,
                                             _dp]),
     ("cr_iterations", ctypes.c_longlong, [_vp]),
+    ("cr_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_longlong]),
     ("cr_set_gamma", ctypes.c_int, [_vp, ctypes.c_double]),
     ("cr_solve_path", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(cr_gap_info)]),
     ("cr_solve_continuation", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -62,6 +62,37 @@ void choose_split(cr_ctx *c) {
     c->grid = (int)std::min<long long>(items, (long long)G);
 }
 
+RefreshArgs refresh_args(const cr_ctx *c) {
+    RefreshArgs r{};
+    r.N = c->N;
+    r.n = c->n;
+    r.period = c->opt.refresh_every;
+    r.segs = c->rf_segs;
+    r.ld = c->ld;
+    r.ldv = c->ldv;
+    for (int i = 0; i < 3; ++i) r.lam[i] = (float *)c->lam[i];
+    r.X = c->X;
+    r.ybar = c->ybar;
+    for (int i = 0; i < 2; ++i) {
+        r.hist_a[i] = c->ha[i];
+        r.hist_b[i] = c->hb[i];
+    }
+    r.r_out = c->rf_r;
+    r.B_out = c->rf_B;
+    r.cpart = c->rf_c;
+    r.blockpart = c->finblk;
+    r.log = c->log;
+    r.yh = c->yh;
+    r.yl = c->yl;
+    r.uh = c->uh;
+    r.ul = c->ul;
+    r.xiT = c->xiT;
+    r.xi_rm = c->xi_rm;
+    r.xT32 = c->xT32;
+    r.st = c->st;
+    return r;
+}
+
 cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */, cudaEvent_t e0,
                             cudaEvent_t e1) {
     const int P = (int)((k - 1) & 1), Q = (int)(k & 1);
@@ -108,6 +139,7 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.p_host = P;
         a.adaptive = c->adaptive ? 1 : 0;
         a.dpart = (float *)c->dpart;
+        a.delta = c->delta ? 1 : 0;
         CR_CUDA(launch_sweep_tc(c->tcm, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
@@ -125,6 +157,8 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.lmaps = c->tm_ld;
         for (int i = 0; i < 3; ++i) a.B[i] = (float *)c->lam[i];
         a.dpart = (float *)c->dpart;
+        a.consumer_wait_ns = c->consumer_wait_ns;
+        a.delta = c->delta ? 1 : 0;
         TmaMaps m = c->tm;
         m.P = &c->tm_lam[P];
         m.Q = &c->tm_lam[Q];
@@ -185,6 +219,7 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
     f.log = c->log;
     f.st = c->st;
     f.init = 0;
+    f.delta = c->delta ? 1 : 0;
     if (c->adaptive) {  // pass 1 decides on the device; the roles of the buffers follow from it
         f.adaptive = 1;
         f.a_new = c->ha_c;
@@ -198,6 +233,7 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
     }
     CR_CUDA(launch_finalize(f, c->stream));
     if (c->adaptive) CR_CUDA(launch_commit(f, c->stream));
+    if (c->delta) CR_CUDA(launch_refresh(refresh_args(c), c->sms, c->stream));
     return CR_OK;
 }
 
@@ -439,8 +475,16 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         c->rowpart = a;
         c->colpart = b;
     }
+    // delta form of the C^T reductions (FP32 TMA sweep), with its exact refresh scratch
+    c->delta = c->opt.refresh_every > 0 && (c->tma || c->tc);
+    if (c->delta) {
+        c->rf_segs = refresh_segments(N, c->sms);
+        CR_TRY(dev_alloc(c, &c->rf_r, (size_t)N));
+        CR_TRY(dev_alloc(c, &c->rf_B, (size_t)N * n));
+        CR_TRY(dev_alloc(c, &c->rf_c, (size_t)c->rf_segs * N));
+    }
     const int gN = (N + 255) / 256;
-    CR_TRY(dev_alloc(c, &c->finblk, (size_t)finalize_blocks(N) * 6));
+    CR_TRY(dev_alloc(c, &c->finblk, (size_t)std::max(finalize_blocks(N) * 6, refresh_finish_blocks(N) * 3)));
     CR_TRY(dev_alloc(c, &c->certblk, (size_t)gN * 2));
     CR_TRY(dev_alloc(c, &c->log, (size_t)kLogCap * 3));
     CR_TRY(dev_alloc(c, &c->st, 1));
@@ -615,6 +659,7 @@ CR_API void cr_default_options(cr_options *o) {
     o->deterministic = 1;
     o->step_rule = CR_STEP_CONSTANT;
     o->upsilon = 2.0;
+    o->refresh_every = 64;
 }
 
 CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int n, const cr_options *opt,
@@ -675,6 +720,10 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
     }
     if (o.tile_cols < 0) {
         set_err("tile_cols must be >= 0");
+        return CR_EINVAL;
+    }
+    if (o.refresh_every < 0) {
+        set_err("refresh_every must be >= 0");
         return CR_EINVAL;
     }
     cr_ctx *c = new (std::nothrow) cr_ctx();
@@ -776,6 +825,23 @@ CR_API cr_status cr_dual_step_timed(cr_ctx *c, int iters, float *sweep_ms, float
     if (sweep_ms) *sweep_ms = sw;
     if (total_ms) *total_ms = tot;
     return s;
+}
+
+CR_API cr_status cr_set_wait_limit(cr_ctx *c, long long consumer_wait_ns) {
+    if (!c || consumer_wait_ns < 0) {
+        set_err("bad argument to cr_set_wait_limit");
+        return CR_EINVAL;
+    }
+    if (!c->tma) {
+        set_err("cr_set_wait_limit applies to the FP32 TMA sweep only");
+        return CR_EUNSUPPORTED;
+    }
+    if (c->gexec) {  // captured graphs hold the old bound
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->consumer_wait_ns = (unsigned long long)consumer_wait_ns;
+    return CR_OK;
 }
 
 CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
@@ -1170,10 +1236,10 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              "\"row_blocks\": %d, \"col_splits\": %d, \"cols_per_split\": %d, \"grid\": %d, "
              "\"ctas_per_sm\": %d, \"sms\": %d, \"pairs\": %.0f, \"lambda_bytes_per_iter\": %.0f, "
              "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d, "
-             "\"step_rule\": %d, \"upsilon\": %.17g, \"sweep\": \"%s\"}",
+             "\"step_rule\": %d, \"upsilon\": %.17g, \"delta\": %d, \"refresh_every\": %d, \"sweep\": \"%s\"}",
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
              pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters, c->opt.step_rule,
-             c->opt.upsilon,
+             c->opt.upsilon, c->delta ? 1 : 0, c->delta ? c->opt.refresh_every : 0,
              c->tc ? "tcgen05"
                    : (c->tma ? "tma" : (c->NP > 32 ? (is_f64(c) ? "wide-fp64" : "wide-fp32") : (is_f64(c) ? "fp64" : "simple"))));
     return CR_OK;

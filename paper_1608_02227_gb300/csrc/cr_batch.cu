@@ -60,9 +60,12 @@ struct cr_batch {
     FinItem *d_fin = nullptr;
     int fin_cap = 0;
     int *d_err = nullptr;
+    int *d_due = nullptr;     // instances whose exact C^T refresh is due ([0] = count)
+    int due_cap = 0;
     std::vector<int> active;  // instance ids in descriptor order
     std::vector<Bucket> buckets;
     int nfin = 0;
+    bool any_delta = false;   // some active instance reduces in delta form
     bool dirty = true;
     int cps = kMinSplit;
     cudaGraphExec_t gexec = nullptr;
@@ -136,6 +139,12 @@ void fill_desc(const cr_batch *b, const cr_ctx *c, InstDesc *d, int id) {
     d->finblk = c->finblk;
     d->log = c->log;
     d->tc = c->tc ? 1 : 0;
+    d->delta = c->delta ? 1 : 0;
+    d->rf_period = c->delta ? c->opt.refresh_every : 0;
+    d->rf_segs = c->rf_segs;
+    d->rf_r = c->rf_r;
+    d->rf_B = c->rf_B;
+    d->rf_c = c->rf_c;
     d->dgroups = c->S * (c->tc ? 2 : 1);  // the tensor-core sweep keeps two groups per split
     if (c->tc) {
         for (int i = 0; i < 3; ++i) {
@@ -155,8 +164,12 @@ void fill_desc(const cr_batch *b, const cr_ctx *c, InstDesc *d, int id) {
 cr_status rebuild(cr_batch *b) {
     drop_graph(b);
     b->active.clear();
+    b->any_delta = false;
     for (int id = 0; id < (int)b->inst.size(); ++id)
-        if (!b->inst[id].done && !b->inst[id].removed) b->active.push_back(id);
+        if (!b->inst[id].done && !b->inst[id].removed) {
+            b->active.push_back(id);
+            b->any_delta = b->any_delta || b->inst[id].c->delta;
+        }
     const int na = (int)b->active.size();
     std::vector<InstDesc> desc(na);
     std::vector<std::vector<WorkItem>> per(kMaxBuckets);
@@ -211,6 +224,7 @@ cr_status rebuild(cr_batch *b) {
     }
     b->nfin = (int)fin.size();
     CR_TRY(grow(&b->d_desc, &b->desc_cap, std::max(1, na)));
+    CR_TRY(grow(&b->d_due, &b->due_cap, na + 1));
     CR_TRY(grow(&b->d_items, &b->items_cap, std::max(1, (int)items.size())));
     CR_TRY(grow(&b->d_fin, &b->fin_cap, std::max(1, b->nfin)));
     if (na) CR_CUDA(cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(InstDesc) * na, cudaMemcpyHostToDevice, b->stream));
@@ -226,6 +240,7 @@ cr_status rebuild(cr_batch *b) {
 
 cr_status enqueue_batch_iteration(cr_batch *b) {
     if (b->active.empty()) return CR_OK;
+    CR_CUDA(cudaMemsetAsync(b->d_due, 0, sizeof(int), b->stream));
     CR_CUDA(cudaEventRecord(b->ev_fork, b->stream));
     for (size_t i = 0; i < b->buckets.size(); ++i) {
         const Bucket &bk = b->buckets[i];
@@ -238,8 +253,9 @@ cr_status enqueue_batch_iteration(cr_batch *b) {
         CR_CUDA(cudaEventRecord(b->ev_join[i], b->aux[i]));
         CR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
     }
-    CR_CUDA(launch_finalize_batch(b->d_desc, b->d_fin, b->nfin, b->stream));
+    CR_CUDA(launch_finalize_batch(b->d_desc, b->d_fin, b->nfin, b->d_due, b->stream));
     if (b->opt.step_rule == CR_STEP_ADAPTIVE) CR_CUDA(launch_commit_batch(b->d_desc, b->d_fin, b->nfin, b->stream));
+    if (b->any_delta) CR_CUDA(launch_refresh_batch(b->d_desc, b->d_due, (int)b->active.size(), b->sms, b->stream));
     return CR_OK;
 }
 
@@ -497,6 +513,8 @@ CR_API long long cr_batch_instance_bytes(long long N, int n) {
     b += 8 * N * n + 8 * N + 4 * 8 * N * (n + 1); // X, ybar, C^T history
     b += 8 * (N + N * n) + 16 * R * N + 8 * gN * 5 + 8 * 3 * 4096 + 4096;
     if (n <= CR_MAX_N_TF32) b += 3 * 2 * ldv * 32 * 4 + 6 * 128 + 4096;  // tensor-core operands and maps
+    // exact C^T refresh scratch: r, B and at most 4 x 152 x 256 / N + 1 column segments (up to 152 SMs)
+    b += 8 * N + 8 * N * n + 8 * (4LL * 152 * 256 + N);
     return b;
 }
 
@@ -551,6 +569,7 @@ CR_API void cr_batch_destroy(cr_batch *b) {
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_fin) cudaFree(b->d_fin);
     if (b->d_err) cudaFree(b->d_err);
+    if (b->d_due) cudaFree(b->d_due);
     for (int i = 0; i < kMaxBuckets; ++i) {
         if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
         if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);

@@ -103,7 +103,8 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         for (int k = ty; k < a.n; k += kFY) {
             const double Bk = a.init ? 0.0 : split_sum<PT>(rowp, a.col_splits, a.N, l, W, k);
             const double xk = a.X[(long long)l * a.n + k];
-            const double bl = r * xk - Bk;
+            // delta form: the partials are of lambda^k - lambda^{k-1} and add to C^T lambda^{k-1}
+            const double bl = (a.delta ? a.b_old[(long long)l * a.n + k] : 0.0) + (r * xk - Bk);
             a.b_new[(long long)l * a.n + k] = bl;
             bpart += bl * bl;
             const double bt = opb * bl - beta * a.b_old[(long long)l * a.n + k];
@@ -131,7 +132,7 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         double cc = 0.0;
 #pragma unroll
         for (int y = 0; y < kFY; ++y) cc += s_c[y][tx];
-        const double al = cc - r;
+        const double al = (a.delta ? a.a_old[l] : 0.0) + (cc - r);
         a.a_new[l] = al;
         const double at = opb * al - beta * a.a_old[l];
         const double y = a.ybar[l] + at;
@@ -213,6 +214,7 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         st->t = tn;
         st->beta = beta;
         st->fin_counter = 0u;
+        if (a.due && a.refresh_period > 0 && k % a.refresh_period == 0) a.due[1 + atomicAdd(a.due, 1)] = a.inst;
         __threadfence();
     }
 }
@@ -270,7 +272,7 @@ __device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int 
     if (valid) {
         for (int kk = ty; kk < a.n; kk += kFY) {
             const long long o = (long long)l * a.n + kk;
-            const double bl = r * a.X[o] - split_sum<PT>(rowp, a.col_splits, a.N, l, W, kk);
+            const double bl = (a.delta ? b1[o] : 0.0) + (r * a.X[o] - split_sum<PT>(rowp, a.col_splits, a.N, l, W, kk));
             a.b_new[o] = bl;
             bpart += bl * bl;
             const double db = bl - (opbo * b1[o] - bo * b2[o]);  // b^k - b~ of lambda~^k
@@ -289,7 +291,7 @@ __device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int 
             bb += s_b[y][tx];
             dbb += s_u[y][tx];
         }
-        const double al = cc - r;
+        const double al = (a.delta ? a1[l] : 0.0) + (cc - r);
         a.a_new[l] = al;
         const double da = al - (opbo * a1[l] - bo * a2[l]);
         const PT *dp = reinterpret_cast<const PT *>(a.dpart);
@@ -369,6 +371,7 @@ __device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int 
             st->ring = st->ring == 0 ? 2 : st->ring - 1;  // the candidate becomes lambda^k
             st->s = st->s * st->upsilon;
             st->accepted = 1;
+            if (a.due && a.refresh_period > 0 && k % a.refresh_period == 0) a.due[1 + atomicAdd(a.due, 1)] = a.inst;
         } else {
             st->s = fmax(st->s / st->upsilon, st->inv_L);
             st->accepted = 0;
@@ -428,7 +431,8 @@ __device__ __forceinline__ void commit_point(const FinArgs &a, const int l) {
 __global__ void commit_kernel(const FinArgs a) { commit_point(a, blockIdx.x * blockDim.x + threadIdx.x); }
 
 // Batched finalize: one CTA per (instance, 32-point block) of the work-list.
-__global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDesc *d, const FinItem *items) {
+__global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDesc *d, const FinItem *items,
+                                                                   int *due) {
     const FinItem it = items[blockIdx.x];
     const InstDesc &D = d[it.inst];
     const long long k = D.st->k + 1;  // index of the iteration being finalized
@@ -456,6 +460,12 @@ __global__ void __launch_bounds__(kFX * kFY) finalize_batch_kernel(const InstDes
     a.xiT = D.xiT;
     a.xT32 = D.xT32;
     a.xi_rm = D.xi_rm;
+    a.delta = D.delta;
+    if (D.delta) {
+        a.due = due;
+        a.inst = it.inst;
+        a.refresh_period = D.rf_period;
+    }
     a.blockpart = D.finblk;
     a.log = D.log;
     a.st = D.st;
@@ -564,9 +574,9 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 int finalize_blocks(int N) { return (int)blocks_for(N, kFX); }
 
-cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s) {
+cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, int *due, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    finalize_batch_kernel<<<nitems, kFX * kFY, 0, s>>>(d, items);
+    finalize_batch_kernel<<<nitems, kFX * kFY, 0, s>>>(d, items, due);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,11 @@ struct cr_ctx {
     // sweep shape
     int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
     bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
+    unsigned long long consumer_wait_ns = 0;  // cr_set_wait_limit (0: the default bound)
+    // C^T in delta form with a periodic exact refresh (cr_refresh.cu)
+    bool delta = false;
+    double *rf_r = nullptr, *rf_B = nullptr, *rf_c = nullptr;
+    int rf_segs = 0;
     CUtensorMap tm_lam[3];
     CUtensorMap *tm_ld = nullptr;  // adaptive step: device copy of tm_lam (roles chosen on the device)
     TmaMaps tm{};

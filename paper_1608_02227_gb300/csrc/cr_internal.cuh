@@ -51,6 +51,8 @@ struct DevState {
     double prev_g;      // g_gamma of the last accepted iterate
     long long sweeps;   // candidate steps taken
     double check_lhs, check_rhs;  // last check: (||da||^2 + ||db||^2/gamma)/s_k <= ||lambda^k - lambda~^k||^2
+    long long refreshed_k;  // iteration of the last exact re-evaluation of C^T lambda (cr_refresh.cu)
+    long long refreshes;    // exact re-evaluations so far
 };
 
 // Roles of the multiplier buffers in the sweep about to run: inputs lambda^{k-1} (p),
@@ -157,6 +159,8 @@ struct TmaSweepArgs {
     float *rowpart;          // S x N x (NP+1)
     float *colpart;          // RB x ld
     int *err;
+    unsigned long long consumer_wait_ns;  // bound of the consumers' data waits (0: the default 2 s)
+    int delta;               // 1: the reductions are of lambda^k - lambda^{k-1} (C^T increments)
 };
 struct TmaMaps {
     const CUtensorMap *P, *Q;            // lambda^{k-1}, lambda^{k-2}: [N][ld], box 128 x R
@@ -186,6 +190,7 @@ struct TcSweepArgs {
     const CUtensorMap *smaps;  // device array: store maps of the same buffers (box 32 x 32)
     int p_host;              // constant step: buffer holding lambda^{k-1}
     int adaptive;
+    int delta;               // 1: the reductions are of lambda^k - lambda^{k-1}
     float *dpart;            // adaptive step: [S][2][N] row sums of (lambda^k - lambda~^k)^2 per epilogue group
 };
 struct TcMaps {
@@ -213,6 +218,9 @@ struct InstDesc {
     CUtensorMap tc_lam_ld[3], tc_lam_st[3];
     CUtensorMap tc_xrh, tc_xrl, tc_xt, tc_y;
     int tc;
+    int delta;                           // reductions of lambda^k - lambda^{k-1} (see cr_refresh.cu)
+    int rf_period, rf_segs;              // delta form: exact refresh every rf_period iterations
+    double *rf_r, *rf_B, *rf_c;          // its scratch (N, N x n, rf_segs x N)
     int dgroups;                         // adaptive step: groups of the row sums in dpart
     float *xi_rm;                        // tensor-core instances: xi rows [2][ldv][32]
     float *lam[3];
@@ -239,7 +247,7 @@ cudaError_t launch_sweep_tc_batch(const InstDesc *d, const WorkItem *w, int nite
 struct FinItem {
     int inst, block;
 };
-cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s);
+cudaError_t launch_finalize_batch(const InstDesc *d, const FinItem *items, int nitems, int *due, cudaStream_t s);
 // adaptive step: the commit of every instance whose candidate was accepted
 cudaError_t launch_commit_batch(const InstDesc *d, const FinItem *items, int nitems, cudaStream_t s);
 
@@ -271,12 +279,38 @@ struct FinArgs {
     double *hist_a[2], *hist_b[2];
     const void *dpart;       // float or double, dgroups x N: row sums of (lambda^k - lambda~^k)^2
     int dgroups;
+    // 1: the partials reduce lambda^k - lambda^{k-1}, so (a,b)^k = (a,b)^{k-1} + their C^T
+    int delta;
+    // batches: when an exact refresh of this instance becomes due (k a multiple of
+    // refresh_period) the last CTA appends inst to the device list due ([0] = count)
+    int *due, inst, refresh_period;
 };
 cudaError_t launch_finalize(const FinArgs &a, cudaStream_t s);
 // adaptive step, pass 2: when the candidate was accepted, store (a,b)^k in the history and
 // build eta(lambda~^{k+1}) for the next sweep; otherwise nothing changes
 cudaError_t launch_commit(const FinArgs &a, cudaStream_t s);
 int finalize_blocks(int N);   // CTAs of the finalize kernel (size of its block-partial buffer / 3)
+
+// ---------------------------------------------------------------- exact C^T refresh (cr_refresh.cu)
+struct RefreshArgs {
+    int N, n, period, segs;
+    long long ld, ldv;
+    float *lam[3];           // the multiplier buffers (lambda^k chosen on the device)
+    const double *X, *ybar;
+    double *hist_a[2], *hist_b[2];
+    double *r_out, *B_out;   // N, N x n scratch
+    double *cpart;           // segs x N scratch
+    double *blockpart;       // refresh_finish_blocks(N) x 3
+    double *log;
+    float *yh, *yl, *uh, *ul, *xiT, *xi_rm;
+    const float *xT32;
+    DevState *st;
+};
+int refresh_segments(int N, int sms);
+int refresh_finish_blocks(int N);
+cudaError_t launch_refresh(const RefreshArgs &a, int sms, cudaStream_t s);
+// batches: the refresh of every instance on the device list due (filled by the batched finalize)
+cudaError_t launch_refresh_batch(const InstDesc *d, const int *due, int max_due, int sms, cudaStream_t s);
 
 // eta(lambda^k) from the history: y = ybar + a, xi = b / gamma (FP64, row-major)
 cudaError_t launch_primal(int N, int n, const double *ybar, const double *a, const double *b,

@@ -252,7 +252,7 @@ struct TcView {
     float *rowpart, *colpart, *dpart;
     const DevState *st;
     long long ld, ldv, c0, c1;
-    int N, n, NP, rb, sp, i0, nch, adaptive;
+    int N, n, NP, rb, sp, i0, nch, adaptive, delta;
 };
 
 __device__ __forceinline__ void tc_bounds(TcView &v, int cols_per_split) {
@@ -274,6 +274,7 @@ struct TcSrcSingle {
         v.P = a->lmaps + bp;
         v.Q = a->lmaps + bq;
         v.Qs = a->smaps + br;
+        v.delta = a->delta;
         v.XRh = XRh, v.XRl = XRl, v.XT = XT, v.Y = Y;
         v.xi_rm = a->xi_rm;
         v.u = a->u;
@@ -312,6 +313,7 @@ struct TcSrcBatch {
         v.P = &D.tc_lam_ld[bp];
         v.Q = &D.tc_lam_ld[bq];
         v.Qs = &D.tc_lam_st[br];
+        v.delta = D.delta;
         v.XRh = &D.tc_xrh, v.XRl = &D.tc_xrl, v.XT = &D.tc_xt, v.Y = &D.tc_y;
         v.xi_rm = D.xi_rm;
         v.u = D.uh;
@@ -336,7 +338,10 @@ struct TcSrcBatch {
 // lambda = max(0, lambda~ + s rho), rho = (u_h - y_h) + (u_l - y_l) + S; the new lambda
 // overwrites P and its TF32 low part overwrites Q (both 128-byte swizzled).  EDGE adds the
 // zeroing of the diagonal and of padding rows and columns.
-template <bool EDGE, bool ADAPT>
+// DELTA: P receives lambda^k (the source of the TMA store) and Qs the full FP32 change
+// lambda^k - lambda^{k-1} (the operand of the C^T reductions in delta form); once the store
+// has read P, the caller replaces P by the TF32 low part of the change.
+template <bool EDGE, bool ADAPT, bool DELTA>
 __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, const float (&v)[kC], int r,
                                           float2 uh2, float2 ul2, float2 beta2, float2 s2, bool rv, int i,
                                           long long j0, int N, float &dsum) {
@@ -374,14 +379,17 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
                 const long long j = j0 + 4 * g + e;
                 if (!rv || j >= N || j == i) l[e] = 0.f;
             }
-            lo[e] = tf32_lo(l[e]);
+            if (!DELTA) lo[e] = tf32_lo(l[e]);
             if (ADAPT) {  // lambda^k - lambda~^k without cancellation: s rho where the step is not clipped
                 const float d = l[e] > 0.f ? sr[e] : -ltv[e];
                 dsum = fmaf(d, d, dsum);
             }
         }
         *reinterpret_cast<float4 *>(P + off) = make_float4(l[0], l[1], l[2], l[3]);
-        *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        if (DELTA)  // lambda^{k-1} is 0 on the diagonal and the padding, as lambda^k is
+            *reinterpret_cast<float4 *>(Qs + off) = make_float4(l[0] - p4.x, l[1] - p4.y, l[2] - p4.z, l[3] - p4.w);
+        else
+            *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
@@ -571,7 +579,12 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     }
                     tc_fence_after();
                     const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
-                    gemm2(tA(ab), st + kOffP, st + kOffQ, st + kOffXT, c > 0);
+                    // A operand (hi, lo): lambda^k in P and its TF32 low part in Q, or in delta form
+                    // the change of lambda in Q and its low part in P
+                    if (it.delta)
+                        gemm2(tA(ab), st + kOffQ, st + kOffP, st + kOffXT, c > 0);
+                    else
+                        gemm2(tA(ab), st + kOffP, st + kOffQ, st + kOffXT, c > 0);
                     mma_commit(&empty[s]);
                     if (c == it.nch - 1) mma_commit(&afull[ab]);
                 }
@@ -652,29 +665,34 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 // a pair with one chunk (odd count at the end of an item) is released for both groups
                 if (lane == 0) bar_arrive_n(&sempty[b], (c + 1 < it.nch || (c & 1)) ? 1u : 2u);
                 float *P = reinterpret_cast<float *>(st + kOffP);
+                float *Qs = reinterpret_cast<float *>(st + kOffQ);
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
-                    float *Qs = reinterpret_cast<float *>(st + kOffQ);
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N) ||
                                       (it.i0 + kM > it.N);
-                    if (it.adaptive) {
-                        if (edge)
-                            epi_chunk<true, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
-                        else
-                            epi_chunk<false, true>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
-                    } else if (edge) {
-                        epi_chunk<true, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
+#define CR_EPI(E, A, D) epi_chunk<E, A, D>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum)
+                    if (it.delta) {
+                        if (it.adaptive) {
+                            if (edge) CR_EPI(true, true, true); else CR_EPI(false, true, true);
+                        } else {
+                            if (edge) CR_EPI(true, false, true); else CR_EPI(false, false, true);
+                        }
+                    } else if (it.adaptive) {
+                        if (edge) CR_EPI(true, true, false); else CR_EPI(false, true, false);
                     } else {
-                        epi_chunk<false, false>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum);
+                        if (edge) CR_EPI(true, false, false); else CR_EPI(false, false, false);
                     }
+#undef CR_EPI
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
                 }
                 __syncwarp();
                 if (lane == 0) {
                     // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
                     if (ok && it.i0 + 32 * q < it.N) tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
-                    bar_arrive(&lamr[s]);
+                    if (!it.delta) bar_arrive(&lamr[s]);
                 }
+                // what the C^T reductions see: lambda^k (P), or its change (Qs) in delta form
+                const float *Red = it.delta ? Qs : P;
                 if (ok) {
                     // column sums of this warp's 32 x 32 block, read back from the new tile:
                     // lane = (row group rg of 8 rows, column group g of 4 columns), then a
@@ -684,7 +702,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
                         const int rr = 32 * q + 8 * rg + t;
-                        const float4 x = *reinterpret_cast<const float4 *>(P + rr * 32 + ((g ^ (rr & 7)) << 2));
+                        const float4 x = *reinterpret_cast<const float4 *>(Red + rr * 32 + ((g ^ (rr & 7)) << 2));
                         ca = __fadd2_rn(ca, make_float2(x.x, x.y));
                         cb = __fadd2_rn(cb, make_float2(x.z, x.w));
                     }
@@ -699,6 +717,25 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     }
                     float *colx = reinterpret_cast<float *>(colx0 + (size_t)s * kColxBytes);
                     if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
+                }
+                if (it.delta) {
+                    // once the store has read lambda^k from P, P takes the TF32 low part of the
+                    // change (the second A operand of GEMM2; the first is the change itself, in Qs)
+                    if (lane == 0) tma_store_wait_read();
+                    __syncwarp();
+                    if (ok) {
+                        const int rx = r & 7;
+#pragma unroll
+                        for (int g = 0; g < kC / 4; ++g) {
+                            const int off = r * 32 + ((g ^ rx) << 2);
+                            const float4 d = *reinterpret_cast<const float4 *>(Qs + off);
+                            *reinterpret_cast<float4 *>(P + off) =
+                                make_float4(tf32_lo(d.x), tf32_lo(d.y), tf32_lo(d.z), tf32_lo(d.w));
+                        }
+                        fence_async_smem();
+                    }
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&lamr[s]);
                 }
                 __syncwarp();
                 // last warp through: column partials in quarter order

@@ -54,15 +54,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false when the CTA is aborting or the wait ran out (then abort is set).
+// A bound shorter than the default (the failure-path hook) polls with the non-blocking test,
+// so that a blocking try_wait cannot outlast it.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int *gerr) {
+                                          int *gerr, unsigned long long limit_ns = kWaitNs) {
+    if (limit_ns < kWaitNs) {
+        const uint64_t t0 = globaltimer();
+        for (;;) {
+            if (mbar_test_wait(bar, parity)) return true;
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 >= limit_ns) {
+                *abort_flag = 1;
+                atomicExch(gerr, CR_ETIMEOUT);
+                return false;
+            }
+        }
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicExch(gerr, CR_ETIMEOUT);
             return false;
@@ -100,6 +125,7 @@ struct TmaShape {
 // Per-item view of the data a work item needs (tensor maps, pointers, tile bounds).
 struct ItemView {
     const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
+    int delta;               // reduce lambda^k - lambda^{k-1} instead of lambda^k
     float *Qp;               // lambda^k is written here
     float *dpart;            // adaptive step: row sums of (lambda^k - lambda~^k)^2, [S][N]
     long long ld, c0, c1;
@@ -113,6 +139,9 @@ struct SrcSingle {
     const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
     TmaSweepArgs a;
     __device__ __forceinline__ int count() const { return a.row_blocks * a.col_splits; }
+    __device__ __forceinline__ unsigned long long consumer_wait_ns() const {
+        return a.consumer_wait_ns ? a.consumer_wait_ns : kWaitNs;
+    }
     __device__ __forceinline__ void prefetch() const {
         prefetch_tmap(P);
         prefetch_tmap(Q);
@@ -124,6 +153,7 @@ struct SrcSingle {
     __device__ __forceinline__ ItemView view(int item, int rows) const {
         ItemView v;
         v.P = P; v.Q = Q; v.X = X; v.Y = Y; v.Xi = Xi; v.U = U;
+        v.delta = a.delta;
         v.Qp = a.Q;
         v.dpart = a.dpart;
         if (a.adaptive) {  // buffer roles rotate on the device (three buffers)
@@ -156,6 +186,7 @@ struct SrcBatch {
     const WorkItem *w;
     int n;
     __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ unsigned long long consumer_wait_ns() const { return kWaitNs; }
     __device__ __forceinline__ void prefetch() const {}
     __device__ __forceinline__ ItemView view(int item, int rows) const {
         const WorkItem wi = w[item];
@@ -166,6 +197,7 @@ struct SrcBatch {
         v.P = &D.tm_lam[bp];
         v.Q = &D.tm_lam[bq];
         v.X = &D.tm_x; v.Y = &D.tm_y; v.Xi = &D.tm_xi; v.U = &D.tm_u;
+        v.delta = D.delta;
         v.Qp = D.lam[br];
         v.dpart = D.dpart;
         v.ld = D.ld;
@@ -224,7 +256,9 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                 for (long long j0 = c0; j0 < c1; j0 += kChunk, ++fill) {
                     const int s = fill % STAGES;
                     const uint32_t ph = (fill / STAGES) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) {
+                    // after an abort no new copy is issued: a consumer that gave up on a stage
+                    // releases it with that stage's copy possibly still in flight
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err) || *abort_flag) {
                         ok = false;
                         break;
                     }
@@ -255,6 +289,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
     } else {
         // ------------------------------------------------------------ consumers
         const float2 m1 = make_float2(-1.f, -1.f);
+        const unsigned long long cwait = src.consumer_wait_ns();
         uint32_t fill = 0, item_no = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++item_no) {
             const ItemView v = src.view(item, kRowsT);
@@ -263,6 +298,9 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
             const float beta = (float)v.st->beta;
             const float sstep = (float)v.st->s;
             const float2 beta2 = make_float2(beta, beta), s2 = make_float2(sstep, sstep);
+            // the reductions see lambda^k - dsub * lambda^{k-1}: the C^T increments in delta form
+            const float dsub = v.delta ? 1.f : 0.f;
+            const float2 dsub2 = make_float2(-dsub, -dsub);
             const float *rbuf = rowbuf + (item_no % XB) * S::ROWBUF_FLOATS;
             const float *xis = rbuf;                  // [NP][kRowsT]
             const float *ush = rbuf + NP * kRowsT;    // [2][kRowsT]: u hi, u lo
@@ -285,7 +323,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
             for (long long j0 = c0; j0 < c1; j0 += kChunk, ++fill) {
                 const int s = fill % STAGES;
                 const uint32_t ph = (fill / STAGES) & 1u;
-                const bool ok = mbar_wait(&full[s], ph, abort_flag, err);
+                const bool ok = mbar_wait(&full[s], ph, abort_flag, err, cwait);
                 float *st = stages + (size_t)s * (S::STAGE_BYTES / 4);
                 if (ok) {
                     float lam[MR][4];
@@ -364,6 +402,13 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                         if (4 * lane + j0 < c1 && i0 + rloc + r < NN)
                             __stcs(reinterpret_cast<float4 *>(v.Qp + (long long)(i0 + rloc + r) * ld + j0 + 4 * lane),
                                    make_float4(lam[r][0], lam[r][1], lam[r][2], lam[r][3]));
+                        // from here on lam holds what the reductions sum: lambda^k, or its change
+                        // (lambda^{k-1} is 0 on the diagonal and the padding, as lambda^k is)
+                        {
+                            const float2 da = __ffma2_rn(dsub2, pa, make_float2(lam[r][0], lam[r][1]));
+                            const float2 db = __ffma2_rn(dsub2, pb, make_float2(lam[r][2], lam[r][3]));
+                            lam[r][0] = da.x, lam[r][1] = da.y, lam[r][2] = db.x, lam[r][3] = db.y;
+                        }
                         cs01 = __fadd2_rn(cs01, make_float2(lam[r][0], lam[r][1]));
                         cs23 = __fadd2_rn(cs23, make_float2(lam[r][2], lam[r][3]));
                     }
