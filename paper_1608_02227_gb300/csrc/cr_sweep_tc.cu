@@ -46,7 +46,7 @@ constexpr int kC = 32;        // columns per chunk (GEMM2 K)
 constexpr int kK = 32;        // point dimension padded (GEMM1 K)
 constexpr int kStages = 4;    // ring of lambda / transposed-point stages
 constexpr int kXr = 2;        // ring of point-row pair tiles (GEMM1 B operand)
-constexpr int kSBufs = 4;     // pair S tiles in tensor memory
+constexpr int kSBufs = 3;     // pair S tiles in tensor memory
 constexpr int kTiles = kM * kC * 4;             // bytes of one 128 x 32 FP32 tile (16 KB)
 constexpr int kXtBytes = 2 * kK * kC * 4;       // transposed points, hi and lo rows (64 x 32, 8 KB)
 // stage layout (bytes): P | Q | XT; y (hi 32, lo 32) and the column partials of each
@@ -66,10 +66,12 @@ constexpr size_t kSmemData =
 constexpr size_t kSmem = 1024 + kSmemData + 512;
 static_assert(kStageBytes % 1024 == 0 && kXrBytes % 1024 == 0, "swizzled tiles keep 1024-byte alignment");
 static_assert(kSmem <= 232448, "shared memory budget");
-// tensor memory: S[b] (64 columns each) at 64 b, ACC[0..1] (64 each) at 256, XI[0..1]
-// (hi 32 + lo 32 each) at 384
+// tensor memory: S[b] (64 columns each) at 64 b, ACC[0..1] (64 each) at 192, XI[0..1]
+// (hi 32 + lo 32 each) at 320, DLO[0..1] (32 each; delta form: the TF32 low part of the change of
+// lambda, the second A operand of GEMM2, one slot per epilogue group) at 448
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 128u;
+constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 128u, kColDlo = kColXi + 128u;
+static_assert(kColDlo + 64u <= kTmemCols, "tensor-memory budget");
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
 constexpr int kTcDevices = 128;
@@ -202,6 +204,14 @@ __device__ __forceinline__ void gemm2(uint32_t tmem_d, uint32_t ah, uint32_t al,
         for (int k = 0; k < kC / 8; ++k) mma_ss(tmem_d, sdesc(A + 32 * k), sdesc(b + 32 * k), acc_first || p > 0 || k > 0);
     }
 }
+// GEMM2 in delta form: the change of lambda (FP32, read as TF32) from shared memory and its
+// TF32 low part from tensor memory (columns dlo .. dlo + 31)
+__device__ __forceinline__ void gemm2_delta(uint32_t tmem_d, uint32_t ah, uint32_t dlo, uint32_t b, bool acc_first) {
+#pragma unroll
+    for (int k = 0; k < kC / 8; ++k) mma_ss(tmem_d, sdesc(ah + 32 * k), sdesc(b + 32 * k), acc_first || k > 0);
+#pragma unroll
+    for (int k = 0; k < kC / 8; ++k) mma_ts(tmem_d, dlo + 8u * k, sdesc(b + 32 * k), true);
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
     asm volatile(
@@ -226,6 +236,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
 }
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
     asm volatile(
@@ -338,17 +358,18 @@ struct TcSrcBatch {
 // lambda = max(0, lambda~ + s rho), rho = (u_h - y_h) + (u_l - y_l) + S; the new lambda
 // overwrites P and its TF32 low part overwrites Q (both 128-byte swizzled).  EDGE adds the
 // zeroing of the diagonal and of padding rows and columns.
-// DELTA: P receives lambda^k (the source of the TMA store) and Qs the full FP32 change
-// lambda^k - lambda^{k-1} (the operand of the C^T reductions in delta form); once the store
-// has read P, the caller replaces P by the TF32 low part of the change.
-template <bool EDGE, bool ADAPT, bool DELTA>
-__device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, const float (&v)[kC], int r,
-                                          float2 uh2, float2 ul2, float2 beta2, float2 s2, bool rv, int i,
-                                          long long j0, int N, float &dsum) {
+// DELTA: P receives lambda^k (the source of the TMA store), Qs the full FP32 change
+// lambda^k - lambda^{k-1} (the operand of the C^T reductions in delta form) and dlo its TF32 low
+// part, which the caller moves to tensor memory.
+// One half of the chunk row (16-byte groups 4 HALF .. 4 HALF + 3); dlo receives the half's low parts.
+template <bool EDGE, bool ADAPT, bool DELTA, int HALF>
+__device__ __forceinline__ void epi_half(float *P, float *Qs, const float *Y, const float (&v)[kC], int r,
+                                         float2 uh2, float2 ul2, float2 beta2, float2 s2, bool rv, int i,
+                                         long long j0, int N, float &dsum, float (&dlo)[kC / 2]) {
     const float2 m1 = make_float2(-1.f, -1.f);
     const int rx = r & 7;
 #pragma unroll
-    for (int g = 0; g < kC / 4; ++g) {  // 16-byte chunk g of the row sits at position g ^ (r % 8)
+    for (int g = 4 * HALF; g < 4 * HALF + 4; ++g) {  // 16-byte chunk g of the row sits at position g ^ (r % 8)
         const int off = r * 32 + ((g ^ rx) << 2);
         const float4 p4 = *reinterpret_cast<const float4 *>(P + off);
         const float4 q4 = *reinterpret_cast<const float4 *>(Qs + off);
@@ -386,10 +407,14 @@ __device__ __forceinline__ void epi_chunk(float *P, float *Qs, const float *Y, c
             }
         }
         *reinterpret_cast<float4 *>(P + off) = make_float4(l[0], l[1], l[2], l[3]);
-        if (DELTA)  // lambda^{k-1} is 0 on the diagonal and the padding, as lambda^k is
-            *reinterpret_cast<float4 *>(Qs + off) = make_float4(l[0] - p4.x, l[1] - p4.y, l[2] - p4.z, l[3] - p4.w);
-        else
+        if (DELTA) {  // lambda^{k-1} is 0 on the diagonal and the padding, as lambda^k is
+            const float d[4] = {l[0] - p4.x, l[1] - p4.y, l[2] - p4.z, l[3] - p4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dlo[4 * (g - 4 * HALF) + e] = tf32_lo(d[e]);
+            *reinterpret_cast<float4 *>(Qs + off) = make_float4(d[0], d[1], d[2], d[3]);
+        } else {
             *reinterpret_cast<float4 *>(Qs + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        }
     }
 }
 
@@ -414,7 +439,8 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     uint64_t *rempty = rfull + kXr;         // [kXr] GEMM1 that read them done
     uint64_t *afull = rempty + kXr;         // [2] accumulator of an item complete
     uint64_t *aempty = afull + 2;           // [2] accumulator read (one per warp)
-    uint64_t *fin = aempty + 2;             // all MMAs done (teardown)
+    uint64_t *dloe = aempty + 2;            // [2] delta form: the GEMM2 that read a group's DLO slot done
+    uint64_t *fin = dloe + 2;               // all MMAs done (teardown)
     int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
     volatile int *abort_flag = ticket + kStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
@@ -438,6 +464,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             bar_init(&xempty[b], 1);
             bar_init(&afull[b], 1);
             bar_init(&aempty[b], kEpiWarps);
+            bar_init(&dloe[b], 1);
         }
         for (int b = 0; b < kXr; ++b) {
             bar_init(&rfull[b], 1);
@@ -460,6 +487,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     auto tS = [tmem](int b) { return tmem + 64u * (uint32_t)b; };
     auto tA = [tmem](int b) { return tmem + kColAcc + 64u * (uint32_t)b; };
     auto tX = [tmem](int b) { return tmem + kColXi + 64u * (uint32_t)b; };
+    auto tD = [tmem](int h) { return tmem + kColDlo + 32u * (uint32_t)h; };
 
     if (warp == 0) {
         // ---------------------------------------------------------------- stage producer
@@ -580,11 +608,13 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     tc_fence_after();
                     const uint32_t st = su32(stage0 + (size_t)s * kStageBytes);
                     // A operand (hi, lo): lambda^k in P and its TF32 low part in Q, or in delta form
-                    // the change of lambda in Q and its low part in P
-                    if (it.delta)
-                        gemm2(tA(ab), st + kOffQ, st + kOffP, st + kOffXT, c > 0);
-                    else
+                    // the change of lambda in Q and its low part in the chunk's group's DLO slot
+                    if (it.delta) {
+                        gemm2_delta(tA(ab), st + kOffQ, tD(c & 1), st + kOffXT, c > 0);
+                        mma_commit(&dloe[c & 1]);
+                    } else {
                         gemm2(tA(ab), st + kOffP, st + kOffQ, st + kOffXT, c > 0);
+                    }
                     mma_commit(&empty[s]);
                     if (c == it.nch - 1) mma_commit(&afull[ab]);
                 }
@@ -632,7 +662,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             if (lane == 0) bar_arrive(&xfull[xb]);
             return ok;
         };
-        uint32_t fill = 0, itn = 0, pair = 0;
+        uint32_t fill = 0, itn = 0, pair = 0, dlo_use = 0;
         bool ok = true;
         if (h == 0 && blockIdx.x < items) ok = put_xi(blockIdx.x, 0);
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
@@ -666,11 +696,31 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 if (lane == 0) bar_arrive_n(&sempty[b], (c + 1 < it.nch || (c & 1)) ? 1u : 2u);
                 float *P = reinterpret_cast<float *>(st + kOffP);
                 float *Qs = reinterpret_cast<float *>(st + kOffQ);
+                if (it.delta) {
+                    // this group's DLO slot is free once the GEMM2 of its previous chunk is done
+                    ok = __all_sync(0xffffffffu, ok && slot_wait(&dloe[h], dlo_use, abort_flag, err));
+                    ++dlo_use;
+                }
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N) ||
                                       (it.i0 + kM > it.N);
-#define CR_EPI(E, A, D) epi_chunk<E, A, D>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum)
+                    // each half of the row at a time; in delta form the half's low parts go to
+                    // this warp's lane quarter of the group's DLO slot right away
+#define CR_EPI(E, A, D)                                                                                \
+    do {                                                                                               \
+        float dlo[kC / 2];                                                                             \
+        epi_half<E, A, D, 0>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum, dlo);         \
+        if (D) {                                                                                       \
+            tc_fence_after();                                                                          \
+            tmem_st16(tD(h) + lq, dlo);                                                                \
+        }                                                                                              \
+        epi_half<E, A, D, 1>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum, dlo);         \
+        if (D) {                                                                                       \
+            tmem_st16(tD(h) + lq + 16u, dlo);                                                          \
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");                               \
+        }                                                                                              \
+    } while (0)
                     if (it.delta) {
                         if (it.adaptive) {
                             if (edge) CR_EPI(true, true, true); else CR_EPI(false, true, true);
@@ -685,11 +735,12 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
 #undef CR_EPI
                     fence_async_smem();  // make the tiles visible to the tensor cores and the TMA store
                 }
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
                     // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
                     if (ok && it.i0 + 32 * q < it.N) tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
-                    if (!it.delta) bar_arrive(&lamr[s]);
+                    bar_arrive(&lamr[s]);
                 }
                 // what the C^T reductions see: lambda^k (P), or its change (Qs) in delta form
                 const float *Red = it.delta ? Qs : P;
@@ -717,25 +768,6 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     }
                     float *colx = reinterpret_cast<float *>(colx0 + (size_t)s * kColxBytes);
                     if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
-                }
-                if (it.delta) {
-                    // once the store has read lambda^k from P, P takes the TF32 low part of the
-                    // change (the second A operand of GEMM2; the first is the change itself, in Qs)
-                    if (lane == 0) tma_store_wait_read();
-                    __syncwarp();
-                    if (ok) {
-                        const int rx = r & 7;
-#pragma unroll
-                        for (int g = 0; g < kC / 4; ++g) {
-                            const int off = r * 32 + ((g ^ rx) << 2);
-                            const float4 d = *reinterpret_cast<const float4 *>(Qs + off);
-                            *reinterpret_cast<float4 *>(P + off) =
-                                make_float4(tf32_lo(d.x), tf32_lo(d.y), tf32_lo(d.z), tf32_lo(d.w));
-                        }
-                        fence_async_smem();
-                    }
-                    __syncwarp();
-                    if (lane == 0) bar_arrive(&lamr[s]);
                 }
                 __syncwarp();
                 // last warp through: column partials in quarter order
