@@ -94,9 +94,9 @@ typedef struct cr_options {
                             function-value restart of the accelerated iteration (not in the paper) */
     int refresh_every;   /* CR_FP32 / CR_MIXED_TF32 with n <= 32: > 0 reduces each sweep's change of the
                             multipliers, (a,b)^k = (a,b)^{k-1} + C^T (lambda^k - lambda^{k-1}) in FP64, and
-                            re-evaluates C^T lambda^k exactly in FP64 from the stored multipliers every
-                            refresh_every iterations; 0 forms C^T lambda^k from FP32 partials every
-                            iteration (default 64) */
+                            re-evaluates C^T lambda^k exactly in FP64 from the stored multipliers at
+                            k = 2 refresh_every, 3 refresh_every, ...; 0 forms C^T lambda^k from FP32
+                            partials every iteration (default 64) */
 } cr_options;
 
 /* Convergence record for eta(lambda^k), the primal of Theorem "rate". */
@@ -240,6 +240,43 @@ CR_API cr_status cr_restore(cr_ctx *ctx, const void *buf, long long bytes);
 
 /* Releases every resource of the context (NULL is ignored). */
 CR_API void cr_destroy(cr_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------
+ * Row sharding over several GPUs.  The per-iteration work of the method is the pass over the
+ * constraints that applies C and C^T (Section 3), and it splits over disjoint sets of
+ * constraints: a shard holds the multipliers of the pairs (i, j) with i in [row0, row0 + rows)
+ * and every j.  Each rank (one GPU) creates one shard; an iteration is
+ *     cr_shard_sweep   -> the caller sums the N + 1 exchange values over all shards ->
+ *     cr_shard_finish,
+ * and afterwards every shard holds the same a = C_y^T lambda^k, y, g_gamma, r_gamma and
+ * <lambda, C eta>, and xi of its own rows.  The constant step of Figure "papg" (the adaptive
+ * check would need a second exchange), C^T formed from the partials every iteration (no
+ * exact refresh across shards), no CUDA graphs, n <= CR_MAX_N_BATCH.  The entry points of a
+ * whole instance (cr_dual_step, cr_solve, cr_gap, cr_primal, ...) return CR_EINVAL on a shard.
+ * ------------------------------------------------------------------------------------ */
+
+/* X: all N x n points, ybar: all N observations (host or device, copied); the shard holds rows
+ * [row0, row0 + rows): row0 a multiple of 128, row0 + rows <= N.  opt as in cr_create (the
+ * step rule must be CR_STEP_CONSTANT: CR_EUNSUPPORTED otherwise).  stream: the stream on which
+ * the caller's exchange runs, or NULL. */
+CR_API cr_status cr_shard_create(const double *X, const double *ybar, long long N, int n, long long row0,
+                                 long long rows, const cr_options *opt, void *stream, cr_ctx **out);
+
+/* Enqueues the next iteration's sweep over the shard's rows and writes into exchange (DEVICE
+ * memory of the context's device, N + 1 FP64) the shard's share of the sums every shard needs:
+ * exchange[l] = sum over the held rows i of lambda_il - [l held] sum_j lambda_lj (summed over all
+ * shards: a_l = c_l - r_l of Definition 1), exchange[N] = sum over the held rows of ||b_l||^2. */
+CR_API cr_status cr_shard_sweep(cr_ctx *ctx, double *exchange);
+
+/* Completes the iteration from exchange summed over all shards (device memory, N + 1 FP64):
+ * C^T lambda^k, the objective values, t and beta, and eta of the next extrapolated point. */
+CR_API cr_status cr_shard_finish(cr_ctx *ctx, const double *exchange);
+
+/* eta(lambda^k) as the shard holds it: y (N, every point) and xi of the held rows (rows x n;
+ * either pointer may be NULL; host or device), and *out (nullable): k, g_gamma, r_gamma,
+ * <lambda, C eta> and |<lambda, C eta>| / r_gamma as rel_gap (the infeasibility term needs a pass
+ * over all constraints and is left at 0).  Synchronises. */
+CR_API cr_status cr_shard_state(cr_ctx *ctx, double *y, double *xi, cr_gap_info *out);
 
 /* ------------------------------------------------------------------------------------
  * Batched solving: many independent instances (uneven N and n) iterate together.  Every

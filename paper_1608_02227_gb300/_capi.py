@@ -112,6 +112,11 @@ _SIGS = [
     ("cr_checkpoint", ctypes.c_int, [_vp, _vp, ctypes.c_longlong]),
     ("cr_restore", ctypes.c_int, [_vp, _vp, ctypes.c_longlong]),
     ("cr_destroy", None, [_vp]),
+    ("cr_shard_create", ctypes.c_int, [_vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                                       ctypes.POINTER(cr_options), _vp, ctypes.POINTER(_vp)]),
+    ("cr_shard_sweep", ctypes.c_int, [_vp, _vp]),
+    ("cr_shard_finish", ctypes.c_int, [_vp, _vp]),
+    ("cr_shard_state", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(cr_gap_info)]),
     ("cr_batch_create", ctypes.c_int, [ctypes.POINTER(cr_options), _vp, ctypes.POINTER(_vp)]),
     ("cr_batch_add", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),

@@ -93,8 +93,9 @@ RefreshArgs refresh_args(const cr_ctx *c) {
     return r;
 }
 
-cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */, cudaEvent_t e0,
-                            cudaEvent_t e1) {
+// The sweep of iteration k (1-based): Steps 2 and 4 and the partials of C^T, over the rows the
+// context holds.
+cr_status enqueue_sweep(cr_ctx *c, long long k, cudaEvent_t e0) {
     const int P = (int)((k - 1) & 1), Q = (int)(k & 1);
     if (e0) CR_CUDA(cudaEventRecord(e0, c->stream));
     if (is_f64(c)) {
@@ -117,6 +118,8 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.adaptive = c->adaptive ? 1 : 0;
         for (int i = 0; i < 3; ++i) a.B[i] = (double *)c->lam[i];
         a.dpart = (double *)c->dpart;
+        a.row0 = c->row0;
+        a.row_end = c->row_end;
         CR_CUDA(launch_sweep_d(c->NP, a, c->grid, c->stream));
     } else if (c->tc) {
         TcSweepArgs a{};
@@ -140,6 +143,8 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.adaptive = c->adaptive ? 1 : 0;
         a.dpart = (float *)c->dpart;
         a.delta = c->delta ? 1 : 0;
+        a.row0 = c->row0;
+        a.row_end = c->row_end;
         CR_CUDA(launch_sweep_tc(c->tcm, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
@@ -159,6 +164,8 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.dpart = (float *)c->dpart;
         a.consumer_wait_ns = c->consumer_wait_ns;
         a.delta = c->delta ? 1 : 0;
+        a.row0 = c->row0;
+        a.row_end = c->row_end;
         TmaMaps m = c->tm;
         m.P = &c->tm_lam[P];
         m.Q = &c->tm_lam[Q];
@@ -187,6 +194,12 @@ cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */
         a.dpart = (float *)c->dpart;
         CR_CUDA(launch_sweep_f(c->NP, a, c->grid, c->stream));
     }
+    return CR_OK;
+}
+
+cr_status enqueue_iteration(cr_ctx *c, long long k /* 1-based iteration index */, cudaEvent_t e0,
+                            cudaEvent_t e1) {
+    CR_TRY(enqueue_sweep(c, k, e0));
     if (e1) CR_CUDA(cudaEventRecord(e1, c->stream));
     FinArgs f{};
     f.N = c->N;
@@ -306,7 +319,8 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     c->tc = c->opt.precision == CR_MIXED_TF32;
     c->tma = !f64 && !c->tc && c->NP <= 32 && !(variant && strcmp(variant, "simple") == 0);
     c->rows = c->tc ? sweep_tc_rows() : (c->tma ? sweep_tma_rows(c->NP) : cfg.rows);
-    c->RB = (N + c->rows - 1) / c->rows;
+    const int LR = c->row_end - c->row0;  // rows of Lambda held (all N, or a shard's)
+    c->RB = (LR + c->rows - 1) / c->rows;
     if (c->tc)
         CR_CUDA(sweep_tc_occupancy(&c->occ));
     else if (c->tma)
@@ -321,6 +335,10 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         return CR_EUNSUPPORTED;
     }
     choose_split(c);
+    if (c->shard && !f64 && !c->tc && !c->tma) {
+        set_err("shards run the FP64, TMA or tensor-core sweep");
+        return CR_EUNSUPPORTED;
+    }
     if (c->adaptive && !f64 && !c->tc && !c->tma && c->NP <= 32) {
         set_err("the adaptive step needs the TMA, tensor-core or FP64 sweep (CR_SWEEP=simple has none)");
         return CR_EUNSUPPORTED;
@@ -389,7 +407,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     }
 
     // multipliers: lambda^0 = lambda^{-1} = 0 (and a zeroed third buffer for the adaptive step)
-    const size_t lam_count = (size_t)N * c->ld;
+    const size_t lam_count = (size_t)LR * c->ld;
     const int nbuf = c->adaptive ? 3 : 2;
     for (int i = 0; i < nbuf; ++i) {
         if (f64) {
@@ -434,8 +452,8 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         memset(hl, 0, sizeof(hl));
         memset(hs, 0, sizeof(hs));
         for (int i = 0; i < nbuf; ++i) {
-            CR_CUDA(make_tmap_2d(&hl[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 128, true));
-            CR_CUDA(make_tmap_2d(&hs[i], (const float *)c->lam[i], c->ld, N, c->ld, 32, 32, true));
+            CR_CUDA(make_tmap_2d(&hl[i], (const float *)c->lam[i], c->ld, LR, c->ld, 32, 128, true));
+            CR_CUDA(make_tmap_2d(&hs[i], (const float *)c->lam[i], c->ld, LR, c->ld, 32, 32, true));
         }
         CR_TRY(dev_alloc(c, &c->tc_ld, 3));
         CR_TRY(dev_alloc(c, &c->tc_st, 3));
@@ -451,7 +469,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
     if (c->tma) {
         memset(c->tm_lam, 0, sizeof(c->tm_lam));
         for (int i = 0; i < nbuf; ++i)
-            CR_CUDA(make_tmap_2d(&c->tm_lam[i], (const float *)c->lam[i], c->ld, N, c->ld, kChunk, c->rows));
+            CR_CUDA(make_tmap_2d(&c->tm_lam[i], (const float *)c->lam[i], c->ld, LR, c->ld, kChunk, c->rows));
         if (c->adaptive) {
             CR_TRY(dev_alloc(c, &c->tm_ld, 3));
             CR_CUDA(cudaMemcpyAsync(c->tm_ld, c->tm_lam, sizeof(c->tm_lam), cudaMemcpyHostToDevice, c->stream));
@@ -664,6 +682,16 @@ CR_API void cr_default_options(cr_options *o) {
 
 CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int n, const cr_options *opt,
                            void *stream, cr_ctx **out) {
+    return create_window(X, ybar, N, n, 0, (int)std::min<long long>(N, 1LL << 30), false, opt, stream, out);
+}
+}  // extern "C"
+
+namespace crh {
+
+// A context over rows [row0, row_end) of Lambda (all N for cr_create, a shard for
+// cr_shard_create).
+cr_status create_window(const double *X, const double *ybar, long long N, int n, int row0, int row_end, bool shard,
+                        const cr_options *opt, void *stream, cr_ctx **out) {
     if (!out) {
         set_err("out is NULL");
         return CR_EINVAL;
@@ -732,6 +760,9 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
         return CR_ENOMEM;
     }
     c->N = (int)N;
+    c->row0 = row0;
+    c->row_end = row_end;
+    c->shard = shard;
     c->n = n;
     c->opt = o;
     c->adaptive = o.step_rule == CR_STEP_ADAPTIVE;
@@ -755,7 +786,15 @@ CR_API cr_status cr_create(const double *X, const double *ybar, long long N, int
     return CR_OK;
 }
 
+}  // namespace crh
+
+extern "C" {
+
 CR_API cr_status cr_dual_step(cr_ctx *c, int iters) {
+    if (c && c->shard) {
+        set_err("cr_dual_step works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || iters < 0) {
         set_err("bad argument to cr_dual_step");
         return CR_EINVAL;
@@ -784,6 +823,10 @@ CR_API cr_status cr_dual_step(cr_ctx *c, int iters) {
 }
 
 CR_API cr_status cr_dual_step_timed(cr_ctx *c, int iters, float *sweep_ms, float *total_ms) {
+    if (c && c->shard) {
+        set_err("cr_dual_step_timed works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || iters < 0) {
         set_err("bad argument to cr_dual_step_timed");
         return CR_EINVAL;
@@ -845,6 +888,10 @@ CR_API cr_status cr_set_wait_limit(cr_ctx *c, long long consumer_wait_ns) {
 }
 
 CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
+    if (c && c->shard) {
+        set_err("cr_gap works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c) {
         set_err("ctx is NULL");
         return CR_EINVAL;
@@ -856,6 +903,10 @@ CR_API cr_status cr_gap(cr_ctx *c, cr_gap_info *out) {
 }
 
 CR_API cr_status cr_solve(cr_ctx *c, double tol, long long max_iter, cr_gap_info *out) {
+    if (c && c->shard) {
+        set_err("cr_solve works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || !(tol >= 0.0) || max_iter < 0) {
         set_err("bad argument to cr_solve");
         return CR_EINVAL;
@@ -875,6 +926,10 @@ CR_API cr_status cr_solve(cr_ctx *c, double tol, long long max_iter, cr_gap_info
 }
 
 CR_API cr_status cr_primal(const cr_ctx *c, double *y, double *xi) {
+    if (c && c->shard) {
+        set_err("cr_primal works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c) {
         set_err("ctx is NULL");
         return CR_EINVAL;
@@ -892,6 +947,10 @@ CR_API cr_status cr_primal(const cr_ctx *c, double *y, double *xi) {
 }
 
 CR_API cr_status cr_lambda(const cr_ctx *c, long long row0, long long rows, double *out, long long ld) {
+    if (c && c->shard) {
+        set_err("cr_lambda works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || !out || row0 < 0 || rows < 0 || row0 + rows > c->N || ld < c->N) {
         set_err("bad argument to cr_lambda");
         return CR_EINVAL;
@@ -1032,6 +1091,10 @@ cr_status data_fingerprint(cr_ctx *c, unsigned long long *fp) {
 }  // namespace crh
 
 CR_API cr_status cr_set_gamma(cr_ctx *c, double gamma) {
+    if (c && c->shard) {
+        set_err("cr_set_gamma works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || !(gamma > 0.0) || !isfinite(gamma)) {
         set_err("bad argument to cr_set_gamma");
         return CR_EINVAL;
@@ -1141,6 +1204,10 @@ CR_API long long cr_checkpoint_bytes(const cr_ctx *c) {
 }
 
 CR_API cr_status cr_checkpoint(cr_ctx *c, void *buf, long long bytes) {
+    if (c && c->shard) {
+        set_err("cr_checkpoint works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || !buf || bytes < cr_checkpoint_bytes(c)) {
         set_err("bad argument to cr_checkpoint");
         return CR_EINVAL;
@@ -1178,6 +1245,10 @@ CR_API cr_status cr_checkpoint(cr_ctx *c, void *buf, long long bytes) {
 }
 
 CR_API cr_status cr_restore(cr_ctx *c, const void *buf, long long bytes) {
+    if (c && c->shard) {
+        set_err("cr_restore works on whole instances; a shard iterates with cr_shard_sweep / cr_shard_finish");
+        return CR_EINVAL;
+    }
     if (!c || !buf || bytes < cr_checkpoint_bytes(c)) {
         set_err("bad argument to cr_restore");
         return CR_EINVAL;

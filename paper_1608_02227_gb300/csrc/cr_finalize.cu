@@ -214,7 +214,8 @@ __device__ __forceinline__ void finalize_body(const FinArgs &a, const int blk, c
         st->t = tn;
         st->beta = beta;
         st->fin_counter = 0u;
-        if (a.due && a.refresh_period > 0 && k % a.refresh_period == 0) a.due[1 + atomicAdd(a.due, 1)] = a.inst;
+        if (a.due && a.refresh_period > 0 && k >= 2 * a.refresh_period && k % a.refresh_period == 0)
+            a.due[1 + atomicAdd(a.due, 1)] = a.inst;
         __threadfence();
     }
 }
@@ -371,7 +372,8 @@ __device__ __forceinline__ void finalize_adapt_body(const FinArgs &a, const int 
             st->ring = st->ring == 0 ? 2 : st->ring - 1;  // the candidate becomes lambda^k
             st->s = st->s * st->upsilon;
             st->accepted = 1;
-            if (a.due && a.refresh_period > 0 && k % a.refresh_period == 0) a.due[1 + atomicAdd(a.due, 1)] = a.inst;
+            if (a.due && a.refresh_period > 0 && k >= 2 * a.refresh_period && k % a.refresh_period == 0)
+                a.due[1 + atomicAdd(a.due, 1)] = a.inst;
         } else {
             st->s = fmax(st->s / st->upsilon, st->inv_L);
             st->accepted = 0;

@@ -13,6 +13,11 @@ struct cr_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int N = 0, n = 0, NP = 0;
+    // rows of Lambda this context holds: [row0, row_end) (a shard of cr_shard_create; 0 and N
+    // otherwise); the buffers hold them from their row 0
+    int row0 = 0, row_end = 0;
+    bool shard = false;
+    double *xch_b = nullptr;     // shard: ||b||^2 block partials of the local rows
     long long ld = 0, ldv = 0;
     cr_options opt{};
     double L = 0.0, a2s2 = 0.0, ybar_rms = 1.0;
@@ -103,6 +108,9 @@ void choose_split(cr_ctx *c);
 cr_status create_impl(cr_ctx *c, const double *X, const double *ybar);
 cr_status fetch_state(const cr_ctx *c, DevState *h);
 cr_status enqueue_iteration(cr_ctx *c, long long k, cudaEvent_t e0, cudaEvent_t e1);
+cr_status enqueue_sweep(cr_ctx *c, long long k, cudaEvent_t e0);
+cr_status create_window(const double *X, const double *ybar, long long N, int n, int row0, int row_end, bool shard,
+                        const cr_options *opt, void *stream, cr_ctx **out);
 cr_status gap_launch(cr_ctx *c);
 cr_status gap_launch_k(cr_ctx *c, long long k);
 cr_status gap_finish(const cr_ctx *c, DevState h, cr_gap_info *out);

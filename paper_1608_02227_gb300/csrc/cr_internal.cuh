@@ -106,6 +106,9 @@ struct SweepArgsF {
 struct SweepArgsD {
     const double *P;
     double *Q;
+    int row0, row_end;       // rows [row0, row_end) of Lambda (a shard: the buffers hold these rows
+                             // from their row 0); row0 = 0, row_end = N for a whole instance
+                             // (read by the FP64 kernel of cr_sweep.cu)
     double *B[3];            // adaptive step: the three multiplier buffers (roles from DevState)
     int adaptive;
     double *dpart;           // adaptive step: S x N row sums of (lambda^k - lambda~^k)^2
@@ -161,6 +164,7 @@ struct TmaSweepArgs {
     int *err;
     unsigned long long consumer_wait_ns;  // bound of the consumers' data waits (0: the default 2 s)
     int delta;               // 1: the reductions are of lambda^k - lambda^{k-1} (C^T increments)
+    int row0, row_end;       // rows [row0, row_end) of Lambda (a shard; 0 and N for a whole instance)
 };
 struct TmaMaps {
     const CUtensorMap *P, *Q;            // lambda^{k-1}, lambda^{k-2}: [N][ld], box 128 x R
@@ -192,6 +196,7 @@ struct TcSweepArgs {
     int adaptive;
     int delta;               // 1: the reductions are of lambda^k - lambda^{k-1}
     float *dpart;            // adaptive step: [S][2][N] row sums of (lambda^k - lambda~^k)^2 per epilogue group
+    int row0, row_end;       // rows [row0, row_end) of Lambda (a shard; 0 and N for a whole instance)
 };
 struct TcMaps {
     CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 64, swizzle

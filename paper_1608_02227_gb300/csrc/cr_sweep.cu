@@ -229,16 +229,19 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
         Rp = a.B[ir];
     }
 
+    // a shard holds rows [row0, row_end) of Lambda from its row 0 on (row_end = N, row0 = 0 for a
+    // whole instance); rows are global everywhere else
+    const long long rbase = (long long)a.row0 * a.ld;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int rb = item / a.col_splits, sp = item % a.col_splits;
-        const int i0 = rb * ROWS;
+        const int i0 = a.row0 + rb * ROWS;
         const long long c0 = (long long)sp * a.cols_per_split;
         const long long c1 = min(c0 + (long long)a.cols_per_split, a.ld);
 
         __syncthreads();
         for (int q = tid; q < NP * ROWS; q += NT) {
             const int k = q / ROWS, r = q - k * ROWS, i = i0 + r;
-            xis[q] = (i < a.N) ? a.xiT[(long long)k * a.ldv + i] : 0.0;
+            xis[q] = (i < a.row_end) ? a.xiT[(long long)k * a.ldv + i] : 0.0;
         }
         int ir[MR];
         bool rv[MR];
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
 #pragma unroll
         for (int r = 0; r < MR; ++r) {
             ir[r] = i0 + warp * MR + r;
-            rv[r] = ir[r] < a.N;
+            rv[r] = ir[r] < a.row_end;
             ur[r] = rv[r] ? a.u[ir[r]] : 0.0;
             rs[r] = 0.0;
             dd[r] = 0.0;
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
 #pragma unroll
             for (int r = 0; r < MR; ++r) {
                 if (rv[r] && cv) {
-                    const long long off = (long long)ir[r] * a.ld + jl;
+                    const long long off = (long long)ir[r] * a.ld + jl - rbase;
                     const double2 p01 = ld_stream2(Pp + off), p23 = ld_stream2(Pp + off + 2);
                     const double2 q01 = ld_stream2(Qp + off), q23 = ld_stream2(Qp + off + 2);
                     p4[r][0] = p01.x; p4[r][1] = p01.y; p4[r][2] = p23.x; p4[r][3] = p23.y;
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_f64_kernel(const SweepArgsD 
                     dd[r] = fma(l - lt, l - lt, dd[r]);  // ||lambda^k - lambda~^k||^2 (adaptive step)
                 }
                 if (rv[r] && cv) {
-                    const long long off = (long long)ir[r] * a.ld + jl;
+                    const long long off = (long long)ir[r] * a.ld + jl - rbase;
                     st_stream2(Rp + off, make_double2(lam[r][0], lam[r][1]));
                     st_stream2(Rp + off + 2, make_double2(lam[r][2], lam[r][3]));
                 }

@@ -273,10 +273,11 @@ struct TcView {
     const DevState *st;
     long long ld, ldv, c0, c1;
     int N, n, NP, rb, sp, i0, nch, adaptive, delta;
+    int row0, row_end;                       // the Lambda buffers hold rows [row0, row_end) from their row 0
 };
 
 __device__ __forceinline__ void tc_bounds(TcView &v, int cols_per_split) {
-    v.i0 = v.rb * kM;
+    v.i0 = v.row0 + v.rb * kM;
     v.c0 = (long long)v.sp * cols_per_split;
     v.c1 = min(v.c0 + (long long)cols_per_split, v.ld);
     v.nch = (int)((v.c1 - v.c0 + kC - 1) / kC);
@@ -308,6 +309,8 @@ struct TcSrcSingle {
         v.n = a->n;
         v.NP = a->NP;
         v.adaptive = a->adaptive;
+        v.row0 = a->row0;
+        v.row_end = a->row_end;
         v.rb = item / a->col_splits;
         v.sp = item - v.rb * a->col_splits;
         tc_bounds(v, a->cols_per_split);
@@ -347,6 +350,8 @@ struct TcSrcBatch {
         v.n = D.n;
         v.NP = D.NP;
         v.adaptive = D.adaptive;
+        v.row0 = 0;
+        v.row_end = D.N;
         v.rb = wi.rb;
         v.sp = wi.sp;
         tc_bounds(v, D.cols_per_split);
@@ -505,8 +510,8 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     }
                     unsigned char *st = stage0 + (size_t)s * kStageBytes;
                     bar_expect(&full[s], kTxStage);
-                    tma_load(st + kOffP, it.P, &full[s], j0, it.i0);
-                    tma_load(st + kOffQ, it.Q, &full[s], j0, it.i0);
+                    tma_load(st + kOffP, it.P, &full[s], j0, it.i0 - it.row0);
+                    tma_load(st + kOffQ, it.Q, &full[s], j0, it.i0 - it.row0);
                     tma_load(st + kOffXT, it.XT, &full[s], j0, 0);
                     tma_load(y0 + (size_t)s * kYBytes, it.Y, &full[s], j0, 0);
                 }
@@ -669,7 +674,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             const TcView it = src.view(item);
             const int ab = itn & 1;
             const int i = it.i0 + r;
-            const bool rv = i < it.N;
+            const bool rv = i < it.row_end;
             const float2 beta2 = make_float2((float)it.st->beta, (float)it.st->beta);
             const float2 s2 = make_float2((float)it.st->s, (float)it.st->s);
             // xi rows of the next item go into the other tensor-memory buffer now, so that
@@ -704,7 +709,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
                     const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N) ||
-                                      (it.i0 + kM > it.N);
+                                      (it.i0 + kM > it.row_end);
                     // each half of the row at a time; in delta form the half's low parts go to
                     // this warp's lane quarter of the group's DLO slot right away
 #define CR_EPI(E, A, D)                                                                                \
@@ -739,7 +744,8 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 __syncwarp();
                 if (lane == 0) {
                     // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
-                    if (ok && it.i0 + 32 * q < it.N) tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q);
+                    if (ok && it.i0 + 32 * q < it.row_end)
+                        tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q - it.row0);
                     bar_arrive(&lamr[s]);
                 }
                 // what the C^T reductions see: lambda^k (P), or its change (Qs) in delta form

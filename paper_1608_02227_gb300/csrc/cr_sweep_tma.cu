@@ -126,6 +126,7 @@ struct TmaShape {
 struct ItemView {
     const CUtensorMap *P, *Q, *X, *Y, *Xi, *U;
     int delta;               // reduce lambda^k - lambda^{k-1} instead of lambda^k
+    int row0, row_end;       // the Lambda buffers hold rows [row0, row_end) from their row 0
     float *Qp;               // lambda^k is written here
     float *dpart;            // adaptive step: row sums of (lambda^k - lambda~^k)^2, [S][N]
     long long ld, c0, c1;
@@ -165,9 +166,11 @@ struct SrcSingle {
         }
         v.ld = a.ld;
         v.N = a.N;
+        v.row0 = a.row0;
+        v.row_end = a.row_end;
         v.rb = item / a.col_splits;
         v.sp = item - v.rb * a.col_splits;
-        v.i0 = v.rb * rows;
+        v.i0 = a.row0 + v.rb * rows;
         v.c0 = (long long)v.sp * a.cols_per_split;
         v.c1 = min(v.c0 + (long long)a.cols_per_split, a.ld);
         v.rowpart = a.rowpart;
@@ -202,6 +205,8 @@ struct SrcBatch {
         v.dpart = D.dpart;
         v.ld = D.ld;
         v.N = D.N;
+        v.row0 = 0;
+        v.row_end = D.N;
         v.rb = wi.rb;
         v.sp = wi.sp;
         v.i0 = wi.rb * rows;
@@ -270,8 +275,8 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                         tma_load_2d(rbuf + NP * kRowsT, v.U, &full[s], i0, 0);
                         first = false;
                     }
-                    tma_load_2d(st, v.P, &full[s], (int)j0, i0);
-                    tma_load_2d(st + S::TILE, v.Q, &full[s], (int)j0, i0);
+                    tma_load_2d(st, v.P, &full[s], (int)j0, i0 - v.row0);
+                    tma_load_2d(st + S::TILE, v.Q, &full[s], (int)j0, i0 - v.row0);
                     tma_load_2d(st + 2 * S::TILE, v.X, &full[s], (int)j0, 0);
                     tma_load_2d(st + 2 * S::TILE + NP * kChunk, v.Y, &full[s], (int)j0, 0);
                 }
@@ -293,7 +298,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
         uint32_t fill = 0, item_no = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++item_no) {
             const ItemView v = src.view(item, kRowsT);
-            const int i0 = v.i0, rb = v.rb, sp = v.sp, NN = v.N;
+            const int i0 = v.i0, rb = v.rb, sp = v.sp, NN = v.N, RE = v.row_end;  // RE: end of the rows held
             const long long c0 = v.c0, c1 = v.c1, ld = v.ld;
             const float beta = (float)v.st->beta;
             const float sstep = (float)v.st->s;
@@ -367,7 +372,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                     }
                     // Steps 4 + 2: lambda~ = P + beta (P - Q); lambda = max(0, lambda~ + s rho)
                     const bool edge = (j0 < (long long)i0 + kRowsT && j0 + kChunk > i0) ||
-                                      (j0 + kChunk > NN) || (i0 + kRowsT > NN);
+                                      (j0 + kChunk > NN) || (i0 + kRowsT > RE);
                     float2 cs01 = make_float2(0.f, 0.f), cs23 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int r = 0; r < MR; ++r) {
@@ -388,7 +393,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const long long j = j0 + 4 * lane + c;
-                                if (i >= NN || j >= NN || j == i) lam[r][c] = 0.f;
+                                if (i >= RE || j >= NN || j == i) lam[r][c] = 0.f;
                             }
                         }
                         if constexpr (ADAPT) {  // s rho where the step is not clipped: no cancellation
@@ -399,8 +404,8 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                             const float e3 = lam[r][3] > 0.f ? srb.y : -ltb.y;
                             dd[r] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd[r]))));
                         }
-                        if (4 * lane + j0 < c1 && i0 + rloc + r < NN)
-                            __stcs(reinterpret_cast<float4 *>(v.Qp + (long long)(i0 + rloc + r) * ld + j0 + 4 * lane),
+                        if (4 * lane + j0 < c1 && i0 + rloc + r < RE)
+                            __stcs(reinterpret_cast<float4 *>(v.Qp + (long long)(i0 + rloc + r - v.row0) * ld + j0 + 4 * lane),
                                    make_float4(lam[r][0], lam[r][1], lam[r][2], lam[r][3]));
                         // from here on lam holds what the reductions sum: lambda^k, or its change
                         // (lambda^{k-1} is 0 on the diagonal and the padding, as lambda^k is)
@@ -484,8 +489,8 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                         vy += __shfl_xor_sync(0xffffffffu, vy, o);
                     }
                     if (lane == 0) {
-                        if (ia < NN) da[k] = vx;
-                        if (ib < NN) db[k] = vy;
+                        if (ia < RE) da[k] = vx;
+                        if (ib < RE) db[k] = vy;
                     }
                 }
                 float vx = rs2[p].x, vy = rs2[p].y;
@@ -495,8 +500,8 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
                     vy += __shfl_xor_sync(0xffffffffu, vy, o);
                 }
                 if (lane == 0) {
-                    if (ia < NN) da[NP] = vx;
-                    if (ib < NN) db[NP] = vy;
+                    if (ia < RE) da[NP] = vx;
+                    if (ib < RE) db[NP] = vy;
                 }
             }
             if constexpr (ADAPT) {
@@ -506,7 +511,7 @@ __device__ __forceinline__ void sweep_body(const Src &src, int *err) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
                     const int i = i0 + rloc + r;
-                    if (lane == 0 && i < NN) v.dpart[(long long)sp * NN + i] = v2;
+                    if (lane == 0 && i < RE) v.dpart[(long long)sp * NN + i] = v2;
                 }
             }
         }
