@@ -20,7 +20,7 @@
 //   warp 10 second producer: the point rows of each chunk pair (hi, lo; 64 x 32 each)
 //           for GEMM1, in their own ring, freed as soon as GEMM1 is done;
 //   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 runs up to
-//           three pairs ahead of GEMM2 (four S tiles in tensor memory), issued as soon as
+//           two pairs ahead of GEMM2 (three S tiles in tensor memory), issued as soon as
 //           its inputs land, so the epilogue does not wait for it;
 //   warps 2-9  epilogue in two groups of four (one warp per tensor-memory lane quarter)
 //           that take the even and the odd chunks of an item, thread = row: reads S from
@@ -66,12 +66,15 @@ constexpr size_t kSmemData =
 constexpr size_t kSmem = 1024 + kSmemData + 512;
 static_assert(kStageBytes % 1024 == 0 && kXrBytes % 1024 == 0, "swizzled tiles keep 1024-byte alignment");
 static_assert(kSmem <= 232448, "shared memory budget");
-// tensor memory: S[b] (64 columns each) at 64 b, ACC[0..1] (64 each) at 192, XI[0..1]
-// (hi 32 + lo 32 each) at 320, DLO[0..1] (32 each; delta form: the TF32 low part of the change of
-// lambda, the second A operand of GEMM2, one slot per epilogue group) at 448
+// tensor memory: S[b] (64 columns each) at 64 b, ACC (64) at 192, XI[0..1] (hi 32 + lo 32
+// each) at 256, DLO[0..3] (32 each; delta form: the TF32 low part of the change of lambda, the
+// second A operand of GEMM2; two slots per epilogue group, used in turn, so that a group does
+// not wait for the GEMM2 of its previous chunk) at 384.  One accumulator is enough: both
+// groups read it at the end of an item before they start on the next one.
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 128u, kColDlo = kColXi + 128u;
-static_assert(kColDlo + 64u <= kTmemCols, "tensor-memory budget");
+constexpr int kAccBufs = 1, kDloBufs = 2;
+constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 64u * kAccBufs, kColDlo = kColXi + 128u;
+static_assert(kColDlo + 64u * kDloBufs <= kTmemCols, "tensor-memory budget");
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
 constexpr int kTcDevices = 128;
@@ -442,10 +445,10 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item that used them done
     uint64_t *rfull = xempty + 2;           // [kXr] point-row pair tiles landed
     uint64_t *rempty = rfull + kXr;         // [kXr] GEMM1 that read them done
-    uint64_t *afull = rempty + kXr;         // [2] accumulator of an item complete
-    uint64_t *aempty = afull + 2;           // [2] accumulator read (one per warp)
-    uint64_t *dloe = aempty + 2;            // [2] delta form: the GEMM2 that read a group's DLO slot done
-    uint64_t *fin = dloe + 2;               // all MMAs done (teardown)
+    uint64_t *afull = rempty + kXr;         // [kAccBufs] accumulator of an item complete
+    uint64_t *aempty = afull + kAccBufs;    // [kAccBufs] accumulator read (one per warp)
+    uint64_t *dloe = aempty + kAccBufs;     // [2 kDloBufs] delta form: the GEMM2 that read a DLO slot done
+    uint64_t *fin = dloe + 2 * kDloBufs;    // all MMAs done (teardown)
     int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
     volatile int *abort_flag = ticket + kStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
@@ -467,10 +470,12 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         for (int b = 0; b < 2; ++b) {
             bar_init(&xfull[b], 4);
             bar_init(&xempty[b], 1);
+        }
+        for (int b = 0; b < kAccBufs; ++b) {
             bar_init(&afull[b], 1);
             bar_init(&aempty[b], kEpiWarps);
-            bar_init(&dloe[b], 1);
         }
+        for (int b = 0; b < 2 * kDloBufs; ++b) bar_init(&dloe[b], 1);
         for (int b = 0; b < kXr; ++b) {
             bar_init(&rfull[b], 1);
             bar_init(&rempty[b], 1);
@@ -492,7 +497,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     auto tS = [tmem](int b) { return tmem + 64u * (uint32_t)b; };
     auto tA = [tmem](int b) { return tmem + kColAcc + 64u * (uint32_t)b; };
     auto tX = [tmem](int b) { return tmem + kColXi + 64u * (uint32_t)b; };
-    auto tD = [tmem](int h) { return tmem + kColDlo + 32u * (uint32_t)h; };
+    auto tD = [tmem](int slot) { return tmem + kColDlo + 32u * (uint32_t)slot; };  // slot kDloBufs h + use % kDloBufs
 
     if (warp == 0) {
         // ---------------------------------------------------------------- stage producer
@@ -553,6 +558,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             uint32_t fill = 0, itn = 0, cur_pair = 0;
+            uint32_t dlo_n[2] = {0u, 0u};  // chunks of each epilogue group so far (DLO slot turns)
             bool ok = true;
             // GEMM1 state: the next pair to issue (flattened index g1_pair)
             int g1_item = blockIdx.x, g1_pc = 0;
@@ -590,7 +596,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             };
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
                 const TcView it = src.view(item);
-                const int ab = itn & 1;
+                const int ab = itn % kAccBufs;
                 for (int c = 0; c < it.nch && ok; ++c, ++fill) {
                     if (c > 0 && (c & 1) == 0) ++cur_pair;
                     // GEMM1 runs ahead by up to kSBufs - 1 pairs: it waits only for the pair
@@ -606,7 +612,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                         ok = false;
                         break;
                     }
-                    if (c == 0 && !slot_wait(&aempty[ab], itn >> 1, abort_flag, err)) {
+                    if (c == 0 && !slot_wait(&aempty[ab], itn / kAccBufs, abort_flag, err)) {
                         ok = false;
                         break;
                     }
@@ -615,8 +621,9 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     // A operand (hi, lo): lambda^k in P and its TF32 low part in Q, or in delta form
                     // the change of lambda in Q and its low part in the chunk's group's DLO slot
                     if (it.delta) {
-                        gemm2_delta(tA(ab), st + kOffQ, tD(c & 1), st + kOffXT, c > 0);
-                        mma_commit(&dloe[c & 1]);
+                        const int slot = kDloBufs * (c & 1) + (int)(dlo_n[c & 1]++ % kDloBufs);
+                        gemm2_delta(tA(ab), st + kOffQ, tD(slot), st + kOffXT, c > 0);
+                        mma_commit(&dloe[slot]);
                     } else {
                         gemm2(tA(ab), st + kOffP, st + kOffQ, st + kOffXT, c > 0);
                     }
@@ -672,7 +679,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         if (h == 0 && blockIdx.x < items) ok = put_xi(blockIdx.x, 0);
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
             const TcView it = src.view(item);
-            const int ab = itn & 1;
+            const int ab = itn % kAccBufs;
             const int i = it.i0 + r;
             const bool rv = i < it.row_end;
             const float2 beta2 = make_float2((float)it.st->beta, (float)it.st->beta);
@@ -701,9 +708,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 if (lane == 0) bar_arrive_n(&sempty[b], (c + 1 < it.nch || (c & 1)) ? 1u : 2u);
                 float *P = reinterpret_cast<float *>(st + kOffP);
                 float *Qs = reinterpret_cast<float *>(st + kOffQ);
+                int dslot = 0;
                 if (it.delta) {
-                    // this group's DLO slot is free once the GEMM2 of its previous chunk is done
-                    ok = __all_sync(0xffffffffu, ok && slot_wait(&dloe[h], dlo_use, abort_flag, err));
+                    // the group's next DLO slot is free once the GEMM2 of the chunk that used it last is done
+                    dslot = kDloBufs * h + (int)(dlo_use % kDloBufs);
+                    ok = __all_sync(0xffffffffu, ok && slot_wait(&dloe[dslot], dlo_use / kDloBufs, abort_flag, err));
                     ++dlo_use;
                 }
                 if (ok) {
@@ -718,11 +727,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         epi_half<E, A, D, 0>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum, dlo);         \
         if (D) {                                                                                       \
             tc_fence_after();                                                                          \
-            tmem_st16(tD(h) + lq, dlo);                                                                \
+            tmem_st16(tD(dslot) + lq, dlo);                                                            \
         }                                                                                              \
         epi_half<E, A, D, 1>(P, Qs, Y, v, r, uh2, ul2, beta2, s2, rv, i, j0, it.N, dsum, dlo);         \
         if (D) {                                                                                       \
-            tmem_st16(tD(h) + lq + 16u, dlo);                                                          \
+            tmem_st16(tD(dslot) + lq + 16u, dlo);                                                      \
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");                               \
         }                                                                                              \
     } while (0)
@@ -804,7 +813,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             // end of item: row partials from the GEMM2 accumulator: columns k < n of the two
             // halves give sum_j lambda_ij x_jk, column n of the first gives sum_j lambda_ij;
             // this group reads columns [16 h, 16 h + 16) of both halves
-            const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn >> 1, abort_flag, err));
+            const bool ok2 = __all_sync(0xffffffffu, ok && bar_wait(&afull[ab], itn / kAccBufs, abort_flag, err));
             float acc[kHalf], acl[kHalf];
             tc_fence_after();
             if (ok2) {
