@@ -60,6 +60,18 @@ void choose_split(cr_ctx *c) {
     }
     const long long items = (long long)c->RB * c->S;
     c->grid = (int)std::min<long long>(items, (long long)G);
+    if (c->tc && c->opt.tile_cols <= 0) {
+        // equal ranges of 32-column chunks: the largest CTA share is at most one chunk above the
+        // average, where whole items leave a tail wave (N = 20000: 9 items of 80 chunks on some
+        // CTAs against 8.26 on average)
+        c->seg = true;
+        c->seg_nchr = (int)((c->ld + 31) / 32);
+        c->seg_total = (long long)c->RB * c->seg_nchr;
+        c->grid = (int)std::min<long long>(c->seg_total, (long long)G);
+        const long long tmin = c->seg_total / c->grid;
+        c->S = (int)((c->seg_nchr + tmin - 1) / tmin + 1);
+        c->cps = (int)std::min<long long>(tmin * 32, c->ld);
+    }
 }
 
 RefreshArgs refresh_args(const cr_ctx *c) {
@@ -145,6 +157,9 @@ cr_status enqueue_sweep(cr_ctx *c, long long k, cudaEvent_t e0) {
         a.delta = c->delta ? 1 : 0;
         a.row0 = c->row0;
         a.row_end = c->row_end;
+        a.seg = c->seg ? 1 : 0;
+        a.seg_nchr = c->seg_nchr;
+        a.seg_total = c->seg_total;
         CR_CUDA(launch_sweep_tc(c->tcm, a, c->grid, c->stream));
     } else if (c->tma) {
         TmaSweepArgs a{};
@@ -440,6 +455,8 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
             CR_TRY(dev_alloc(c, &p, (size_t)c->dgroups * N));
             c->dpart = p;
         }
+        // slots no sweep item writes (fewer pieces in a row block than S) stay zero
+        CR_CUDA(cudaMemsetAsync(c->dpart, 0, (size_t)c->dgroups * N * tsz, c->stream));
     }
     if (c->tc) {
         const size_t rm = (size_t)c->ldv * 32;
@@ -461,8 +478,8 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         memcpy(c->tc_lam_st, hs, sizeof(hs));
         CR_CUDA(cudaMemcpyAsync(c->tc_ld, c->tc_lam_ld, sizeof(hl), cudaMemcpyHostToDevice, c->stream));
         CR_CUDA(cudaMemcpyAsync(c->tc_st, c->tc_lam_st, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
-        CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 64, true));
-        CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 64, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 128, true));
+        CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 128, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));
         CR_CUDA(make_tmap_2d(&c->tcm.Y, c->yh, c->ldv, 2, c->ldv, 32, 2));
     }
@@ -493,6 +510,7 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         c->rowpart = a;
         c->colpart = b;
     }
+    CR_CUDA(cudaMemsetAsync(c->rowpart, 0, rp * tsz, c->stream));  // slots no item writes stay zero
     // delta form of the C^T reductions (FP32 TMA sweep), with its exact refresh scratch
     c->delta = c->opt.refresh_every > 0 && (c->tma || c->tc);
     if (c->delta) {
@@ -1307,10 +1325,11 @@ CR_API cr_status cr_describe(const cr_ctx *c, char *buf, int len) {
              "\"row_blocks\": %d, \"col_splits\": %d, \"cols_per_split\": %d, \"grid\": %d, "
              "\"ctas_per_sm\": %d, \"sms\": %d, \"pairs\": %.0f, \"lambda_bytes_per_iter\": %.0f, "
              "\"L\": %.17g, \"sigma_a2_sq\": %.17g, \"cert_row_splits\": %d, \"graph_iters\": %d, "
-             "\"step_rule\": %d, \"upsilon\": %.17g, \"delta\": %d, \"refresh_every\": %d, \"sweep\": \"%s\"}",
+             "\"step_rule\": %d, \"upsilon\": %.17g, \"delta\": %d, \"refresh_every\": %d, \"equal_chunk_ranges\": %d, "
+             "\"sweep\": \"%s\"}",
              c->N, c->n, c->NP, c->opt.precision, c->ld, c->rows, c->RB, c->S, c->cps, c->grid, c->occ, c->sms,
              pairs, 3.0 * tsz * pairs, c->L, c->a2s2, c->cert_R, c->opt.graph_iters, c->opt.step_rule,
-             c->opt.upsilon, c->delta ? 1 : 0, c->delta ? c->opt.refresh_every : 0,
+             c->opt.upsilon, c->delta ? 1 : 0, c->delta ? c->opt.refresh_every : 0, c->seg ? 1 : 0,
              c->tc ? "tcgen05"
                    : (c->tma ? "tma" : (c->NP > 32 ? (is_f64(c) ? "wide-fp64" : "wide-fp32") : (is_f64(c) ? "fp64" : "simple"))));
     return CR_OK;

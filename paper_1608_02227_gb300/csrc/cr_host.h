@@ -50,6 +50,11 @@ struct cr_ctx {
     int *flag = nullptr;
     // sweep shape
     int rows = 0, RB = 0, S = 0, cps = 0, grid = 0, occ = 0;
+    // tensor-core sweep with the automatic split: CTAs take equal ranges of the RB x seg_nchr
+    // 32-column chunks (S is then the most pieces a row block can be cut into)
+    bool seg = false;
+    int seg_nchr = 0;
+    long long seg_total = 0;
     bool tma = false;            // FP32: TMA-pipelined sweep (cr_sweep_tma.cu)
     unsigned long long consumer_wait_ns = 0;  // cr_set_wait_limit (0: the default bound)
     // C^T in delta form with a periodic exact refresh (cr_refresh.cu)

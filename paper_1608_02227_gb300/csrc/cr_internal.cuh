@@ -197,9 +197,12 @@ struct TcSweepArgs {
     int delta;               // 1: the reductions are of lambda^k - lambda^{k-1}
     float *dpart;            // adaptive step: [S][2][N] row sums of (lambda^k - lambda~^k)^2 per epilogue group
     int row0, row_end;       // rows [row0, row_end) of Lambda (a shard; 0 and N for a whole instance)
+    int seg;                 // 1: each CTA takes an equal range of 32-column chunks in row-block order
+    int seg_nchr;            // 32-column chunks of a row block (seg = 1)
+    long long seg_total;     // row_blocks x seg_nchr (seg = 1)
 };
 struct TcMaps {
-    CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 64, swizzle
+    CUtensorMap XRh, XRl;                // points row-major [ldv][32] hi / lo, box 32 x 128, swizzle
     CUtensorMap XT;                      // points transposed, hi rows (with the ones row) then lo rows [64][ldv], box 32 x 64, swizzle
     CUtensorMap Y;                       // y hi / lo [2][ldv], box 32 x 2
 };

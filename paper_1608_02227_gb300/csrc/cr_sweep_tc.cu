@@ -1,35 +1,38 @@
 // cr_sweep_tc.cu -- the Lambda sweep with both contractions on the tensor cores
 // (CR_MIXED_TF32): Steps 2 and 4 of Figure "papg" (K = N) and the C^T reductions, with
-//     S   = Xi_blk . X_pair^T          (rho_ij = u_i - y_j + S_ij)             [GEMM1]
+//     S   = Xi_blk . X_block^T         (rho_ij = u_i - y_j + S_ij)             [GEMM1]
 //     ACC += Lambda_blk . [X | 1]_chunk    (row sums of Lambda.X and of Lambda)   [GEMM2]
 // as tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory.  TF32 keeps the top
 // 19 bits of each FP32 operand (the hardware truncates), so every operand v is split into
 // hi = v (read as trunc(v)) and lo = v - trunc(v):
 //   GEMM1 forms hi.hi + hi.lo + lo.hi with xi (the A operand) held in tensor memory;
 //   GEMM2 stacks the hi and lo parts of [X | 1] along N (N = 64) and runs the hi and the
-//   lo part of Lambda against it, so the accumulator holds Lambda.[X|1]_hi in columns
-//   0..31 and Lambda.X_lo in columns 32..63 (two products instead of three).
-// A tcgen05.mma with M = 128 costs the same for N = 32 and N = 64, so GEMM1 covers two
-// 32-column chunks at once and GEMM2 the two halves of the operand split.
+//   lo part of Lambda (or of its change, in delta form) against it, so the accumulator holds
+//   Lambda.[X|1]_hi in columns 0..31 and Lambda.X_lo in columns 32..63.
+// A tcgen05.mma kind::tf32 with M = 128 takes the same time at N = 64 and at N = 128 (timed on
+// this kernel: the tensor pipe is paid per instruction, one K step of 8), so GEMM1 covers a
+// block of four 32-column chunks with each instruction (N = 128) and GEMM2 the two halves of
+// the operand split.  GEMM2 (8 instructions a chunk) goes to the tensor pipe before the next
+// block's GEMM1 (12 instructions a block), so a stage is released as soon as its epilogue is
+// done.
 //
 // CTA = 11 warps, one CTA per SM, work items of 128 rows x one column split, walked in
-// chunks of 32 columns (pairs of chunks for GEMM1):
+// chunks of 32 columns (blocks of four chunks for GEMM1):
 //   warp 0  producer: 2-D TMA loads (128-byte swizzle) of the lambda^{k-1}, lambda^{k-2}
 //           tiles (128 x 32), the chunk's transposed points with a row of ones (hi rows
 //           then lo rows; 64 x 32) and y (hi, lo), into a ring of stages;
-//   warp 10 second producer: the point rows of each chunk pair (hi, lo; 64 x 32 each)
-//           for GEMM1, in their own ring, freed as soon as GEMM1 is done;
-//   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 runs up to
-//           two pairs ahead of GEMM2 (three S tiles in tensor memory), issued as soon as
-//           its inputs land, so the epilogue does not wait for it;
+//   warp 10 second producer: the point rows of each block (hi, lo; 128 x 32 each) for
+//           GEMM1, freed as soon as GEMM1 is done;
+//   warp 1  tensor-memory allocation and the single MMA-issuing thread: GEMM1 runs one
+//           block ahead of the epilogue (two S tiles in tensor memory);
 //   warps 2-9  epilogue in two groups of four (one warp per tensor-memory lane quarter)
 //           that take the even and the odd chunks of an item, thread = row: reads S from
 //           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
-//           consumed lambda^{k-1} tile (A operand of GEMM2 and source of the warp's TMA
-//           store of its 32 rows of lambda^k) and its TF32 low part over the lambda^{k-2}
-//           tile, sums its 32 x 32 block of the new tile by columns; the first group also
-//           copies the xi rows of the next item into tensor memory; at the end of an item
-//           both groups read the GEMM2 accumulator (row partials).
+//           consumed lambda^{k-1} tile (source of the warp's TMA store of its 32 rows of
+//           lambda^k) and the A operand of GEMM2 over the lambda^{k-2} tile, sums its
+//           32 x 32 block of the new tile by columns; the first group also copies the xi
+//           rows of the next item into tensor memory; at the end of an item both groups
+//           read the GEMM2 accumulator (row partials).
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -45,8 +48,9 @@ constexpr int kM = 128;       // rows per item (MMA M, tensor-memory lanes)
 constexpr int kC = 32;        // columns per chunk (GEMM2 K)
 constexpr int kK = 32;        // point dimension padded (GEMM1 K)
 constexpr int kStages = 4;    // ring of lambda / transposed-point stages
-constexpr int kXr = 2;        // ring of point-row pair tiles (GEMM1 B operand)
-constexpr int kSBufs = 3;     // pair S tiles in tensor memory
+constexpr int kQ = 4;         // chunks per GEMM1 block (N = 128: a tcgen05.mma costs the same at N = 64)
+constexpr int kXr = 1;        // ring of point-row block tiles (GEMM1 B operand)
+constexpr int kSBufs = 2;     // block S tiles in tensor memory
 constexpr int kTiles = kM * kC * 4;             // bytes of one 128 x 32 FP32 tile (16 KB)
 constexpr int kXtBytes = 2 * kK * kC * 4;       // transposed points, hi and lo rows (64 x 32, 8 KB)
 // stage layout (bytes): P | Q | XT; y (hi 32, lo 32) and the column partials of each
@@ -55,7 +59,7 @@ constexpr int kOffP = 0, kOffQ = kTiles, kOffXT = 2 * kTiles;
 constexpr int kStageBytes = 2 * kTiles + kXtBytes;
 constexpr int kYBytes = 2 * kC * 4, kColxBytes = 4 * kC * 4;
 constexpr int kTxStage = kStageBytes + kYBytes;
-constexpr int kXrHalf = 2 * kC * kK * 4;        // one 64 x 32 point-row tile (8 KB)
+constexpr int kXrHalf = kQ * kC * kK * 4;       // one 128 x 32 point-row tile (16 KB)
 constexpr int kXrBytes = 2 * kXrHalf;           // hi | lo
 constexpr int kEpiWarps = 8;                    // two groups of four (one warp per lane quarter)
 constexpr int kHalf = kC / 2;                   // accumulator columns read by each group
@@ -66,14 +70,15 @@ constexpr size_t kSmemData =
 constexpr size_t kSmem = 1024 + kSmemData + 512;
 static_assert(kStageBytes % 1024 == 0 && kXrBytes % 1024 == 0, "swizzled tiles keep 1024-byte alignment");
 static_assert(kSmem <= 232448, "shared memory budget");
-// tensor memory: S[b] (64 columns each) at 64 b, ACC (64) at 192, XI[0..1] (hi 32 + lo 32
-// each) at 256, DLO[0..3] (32 each; delta form: the TF32 low part of the change of lambda, the
-// second A operand of GEMM2; two slots per epilogue group, used in turn, so that a group does
-// not wait for the GEMM2 of its previous chunk) at 384.  One accumulator is enough: both
-// groups read it at the end of an item before they start on the next one.
+// tensor memory: S[b] (128 columns each: a block of four chunks) at 128 b, ACC (64) at 256,
+// XI[0..1] (hi 32 + lo 32 each) at 320, DLO[0..1] (32 each; delta form: the TF32 low part of
+// the change of lambda, the second A operand of GEMM2, one slot per epilogue group) at 448.
+// One accumulator is enough: both groups read it at the end of an item before they start on
+// the next one.
 constexpr uint32_t kTmemCols = 512;
-constexpr int kAccBufs = 1, kDloBufs = 2;
-constexpr uint32_t kColAcc = 64u * kSBufs, kColXi = kColAcc + 64u * kAccBufs, kColDlo = kColXi + 128u;
+constexpr int kAccBufs = 1, kDloBufs = 1;
+constexpr uint32_t kColS = (uint32_t)(kQ * kC);
+constexpr uint32_t kColAcc = kColS * kSBufs, kColXi = kColAcc + 64u * kAccBufs, kColDlo = kColXi + 128u;
 static_assert(kColDlo + 64u * kDloBufs <= kTmemCols, "tensor-memory budget");
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kSuspendNs = 1000000u;     // a polling thread sleeps in try_wait up to 1 ms
@@ -167,8 +172,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;              // 128-byte swizzle
     return d;
 }
-// kind::tf32, D = F32, A and B TF32 K-major, M = 128, N = 64
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+// kind::tf32, D = F32, A and B TF32 K-major, M = 128, N = 64 (GEMM2) or N = kQ * 32 (GEMM1)
+constexpr uint32_t idesc_tf32(uint32_t n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+constexpr uint32_t kIdesc = idesc_tf32(64), kIdesc1 = idesc_tf32(kColS);
 
 __device__ __forceinline__ void mma_ss(uint32_t tmem_d, uint64_t ad, uint64_t bd, bool acc) {
     asm volatile(
@@ -177,11 +185,12 @@ __device__ __forceinline__ void mma_ss(uint32_t tmem_d, uint64_t ad, uint64_t bd
         "l"(ad), "l"(bd), "r"(kIdesc), "r"((uint32_t)acc)
         : "memory");
 }
-__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, bool acc) {
+__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, bool acc,
+                                       uint32_t idesc = kIdesc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "r"(tmem_a), "l"(bd), "r"(kIdesc), "r"((uint32_t)acc)
+        "r"(tmem_a), "l"(bd), "r"(idesc), "r"((uint32_t)acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -189,13 +198,13 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 // GEMM1: S = xi_hi.x_hi + xi_hi.x_lo + xi_lo.x_hi, xi in tensor memory (hi at column a,
-// lo at a + 32), the pair's point rows in shared memory (hi tile at bh, lo at bl)
+// lo at a + 32), the block's 128 point rows in shared memory (hi tile at bh, lo at bl)
 __device__ __forceinline__ void gemm1(uint32_t tmem_d, uint32_t a, uint32_t bh, uint32_t bl) {
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const uint32_t A = p < 2 ? a : a + 32u, B = p == 1 ? bl : bh;
 #pragma unroll
-        for (int k = 0; k < kK / 8; ++k) mma_ts(tmem_d, A + 8u * k, sdesc(B + 32 * k), p > 0 || k > 0);
+        for (int k = 0; k < kK / 8; ++k) mma_ts(tmem_d, A + 8u * k, sdesc(B + 32 * k), p > 0 || k > 0, kIdesc1);
     }
 }
 // GEMM2: ACC (+)= lambda_hi.[X|1 ; X_lo] + lambda_lo.[X|1 ; X_lo] over the chunk's 32 columns
@@ -286,11 +295,23 @@ __device__ __forceinline__ void tc_bounds(TcView &v, int cols_per_split) {
     v.nch = (int)((v.c1 - v.c0 + kC - 1) / kC);
 }
 
-// One instance: the point maps are kernel parameters; items tile [0, N) x [0, ld).
+// One instance: the point maps are kernel parameters.  Items tile [0, N) x [0, ld) in one of
+// two ways: 128 rows x one column split, dealt to the CTAs in turn (a->seg = 0); or (a->seg = 1)
+// CTA b takes the 32-column chunks [T b / G, T (b + 1) / G) of the T = row_blocks x nchr chunks
+// in row-block order (G CTAs, nchr chunks to a row block), so that no CTA has more than one
+// chunk above the average, and its items are the pieces of that range in each row block.
+// Piece sp of a row block (sp = the CTAs before b that reach into it) writes row-partial slot sp.
 struct TcSrcSingle {
     const CUtensorMap *XRh, *XRl, *XT, *Y;
     const TcSweepArgs *a;
-    __device__ __forceinline__ int count() const { return a->row_blocks * a->col_splits; }
+    __device__ __forceinline__ long long seg_lo(long long b) const { return b * a->seg_total / gridDim.x; }
+    __device__ __forceinline__ int begin() const { return a->seg ? 0 : (int)blockIdx.x; }
+    __device__ __forceinline__ int step() const { return a->seg ? 1 : (int)gridDim.x; }
+    __device__ __forceinline__ int end() const {
+        if (!a->seg) return a->row_blocks * a->col_splits;
+        const long long g0 = seg_lo(blockIdx.x), g1 = seg_lo(blockIdx.x + 1);
+        return g1 > g0 ? (int)((g1 - 1) / a->seg_nchr - g0 / a->seg_nchr + 1) : 0;
+    }
     __device__ __forceinline__ TcView view(int item) const {
         TcView v;
         int bp, bq, br;
@@ -314,9 +335,23 @@ struct TcSrcSingle {
         v.adaptive = a->adaptive;
         v.row0 = a->row0;
         v.row_end = a->row_end;
-        v.rb = item / a->col_splits;
-        v.sp = item - v.rb * a->col_splits;
-        tc_bounds(v, a->cols_per_split);
+        if (a->seg) {
+            const long long g0 = seg_lo(blockIdx.x), g1 = seg_lo(blockIdx.x + 1), T = a->seg_total;
+            const long long rb = g0 / a->seg_nchr + item, rs = rb * a->seg_nchr;
+            const long long cs = max(g0, rs) - rs, ce = min(g1, rs + a->seg_nchr) - rs;
+            // the first CTA whose range holds chunk rs: the largest b' with T b' / G <= rs
+            const long long bfirst = ((rs + 1) * gridDim.x + T - 1) / T - 1;
+            v.rb = (int)rb;
+            v.sp = (int)(blockIdx.x - bfirst);
+            v.i0 = v.row0 + v.rb * kM;
+            v.c0 = cs * kC;
+            v.c1 = min(ce * kC, v.ld);
+            v.nch = (int)(ce - cs);
+        } else {
+            v.rb = item / a->col_splits;
+            v.sp = item - v.rb * a->col_splits;
+            tc_bounds(v, a->cols_per_split);
+        }
         return v;
     }
 };
@@ -329,7 +364,9 @@ struct TcSrcBatch {
     const InstDesc *d;
     const WorkItem *w;
     int n;
-    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ int begin() const { return (int)blockIdx.x; }
+    __device__ __forceinline__ int step() const { return (int)gridDim.x; }
+    __device__ __forceinline__ int end() const { return n; }
     __device__ __forceinline__ TcView view(int item) const {
         const WorkItem wi = w[item];
         const InstDesc &D = d[wi.inst];
@@ -439,11 +476,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
     uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + each warp's lambda^k rows stored (5 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
-    uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a pair in S[b]
-    uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by both epilogue groups (8 arrivals)
+    uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a block in S[b]
+    uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by the epilogue (4 arrivals per chunk)
     uint64_t *xfull = sempty + kSBufs;      // [2] xi rows of an item in tensor memory (4 arrivals)
     uint64_t *xempty = xfull + 2;           // [2] all GEMM1 of the item that used them done
-    uint64_t *rfull = xempty + 2;           // [kXr] point-row pair tiles landed
+    uint64_t *rfull = xempty + 2;           // [kXr] point-row block tiles landed
     uint64_t *rempty = rfull + kXr;         // [kXr] GEMM1 that read them done
     uint64_t *afull = rempty + kXr;         // [kAccBufs] accumulator of an item complete
     uint64_t *aempty = afull + kAccBufs;    // [kAccBufs] accumulator read (one per warp)
@@ -454,7 +491,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int items = src.count();
+    const int ibeg = src.begin(), iend = src.end(), istep = src.step();  // this CTA's items
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -465,7 +502,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         }
         for (int b = 0; b < kSBufs; ++b) {
             bar_init(&sfull[b], 1);
-            bar_init(&sempty[b], kEpiWarps);
+            bar_init(&sempty[b], 4 * kQ);
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(&xfull[b], 4);
@@ -494,7 +531,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    auto tS = [tmem](int b) { return tmem + 64u * (uint32_t)b; };
+    auto tS = [tmem](int b) { return tmem + kColS * (uint32_t)b; };
     auto tA = [tmem](int b) { return tmem + kColAcc + 64u * (uint32_t)b; };
     auto tX = [tmem](int b) { return tmem + kColXi + 64u * (uint32_t)b; };
     auto tD = [tmem](int slot) { return tmem + kColDlo + 32u * (uint32_t)slot; };  // slot kDloBufs h + use % kDloBufs
@@ -504,7 +541,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         if (lane == 0) {
             uint32_t fill = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            for (int item = ibeg; item < iend && ok; item += istep) {
                 const TcView it = src.view(item);
                 for (int c = 0; c < it.nch; ++c, ++fill) {
                     const int s = fill % kStages;
@@ -533,11 +570,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
         if (lane == 0) {
             uint32_t pf = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            for (int item = ibeg; item < iend && ok; item += istep) {
                 const TcView it = src.view(item);
-                for (int pc = 0; 2 * pc < it.nch; ++pc, ++pf) {
+                for (int bc = 0; kQ * bc < it.nch; ++bc, ++pf) {
                     const int x = pf % kXr;
-                    const int j0 = (int)(it.c0 + (long long)pc * 2 * kC);
+                    const int j0 = (int)(it.c0 + (long long)bc * kQ * kC);
                     if (!slot_wait(&rempty[x], pf / kXr, abort_flag, err)) {
                         ok = false;
                         break;
@@ -557,54 +594,50 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t fill = 0, itn = 0, cur_pair = 0;
+            uint32_t fill = 0, itn = 0, cur_blk = 0;
             uint32_t dlo_n[2] = {0u, 0u};  // chunks of each epilogue group so far (DLO slot turns)
             bool ok = true;
-            // GEMM1 state: the next pair to issue (flattened index g1_pair)
-            int g1_item = blockIdx.x, g1_pc = 0;
-            uint32_t g1_pair = 0, g1_itn = 0;
-            auto g1_norm = [&](void) -> bool {  // advance to a valid (item, pair); false at the end
-                while (g1_item < items) {
-                    if (2 * g1_pc < src.view(g1_item).nch) return true;
-                    g1_item += gridDim.x;
-                    g1_pc = 0;
+            // GEMM1 state: the next block to issue (flattened index g1_blk), its item and chunk count
+            int g1_item = ibeg, g1_bc = 0, g1_nch = ibeg < iend ? src.view(ibeg).nch : 0;
+            uint32_t g1_blk = 0, g1_itn = 0;
+            auto g1_norm = [&](void) -> bool {  // advance to a valid (item, block); false at the end
+                while (g1_item < iend) {
+                    if (kQ * g1_bc < g1_nch) return true;
+                    g1_item += istep;
+                    g1_bc = 0;
                     ++g1_itn;
+                    if (g1_item < iend) g1_nch = src.view(g1_item).nch;
                 }
                 return false;
             };
             auto g1_ready = [&](void) -> bool {  // inputs of the next GEMM1 present (no waiting)
-                const int x = g1_pair % kXr, b = g1_pair % kSBufs;
-                if (!bar_test(&rfull[x], (g1_pair / kXr) & 1u)) return false;
-                if (g1_pc == 0 && !bar_test(&xfull[g1_itn & 1], (g1_itn >> 1) & 1u)) return false;
-                return g1_pair < (uint32_t)kSBufs || bar_test(&sempty[b], (g1_pair / kSBufs - 1) & 1u);
+                const int x = g1_blk % kXr, b = g1_blk % kSBufs;
+                if (!bar_test(&rfull[x], (g1_blk / kXr) & 1u)) return false;
+                if (g1_bc == 0 && !bar_test(&xfull[g1_itn & 1], (g1_itn >> 1) & 1u)) return false;
+                return g1_blk < (uint32_t)kSBufs || bar_test(&sempty[b], (g1_blk / kSBufs - 1) & 1u);
             };
             auto issue_gemm1 = [&](void) -> bool {
-                const int it_nch = src.view(g1_item).nch;
-                const int x = g1_pair % kXr, b = g1_pair % kSBufs, xb = g1_itn & 1;
-                if (!bar_wait(&rfull[x], g1_pair / kXr, abort_flag, err)) return false;
-                if (g1_pc == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, err)) return false;
-                if (!slot_wait(&sempty[b], g1_pair / kSBufs, abort_flag, err)) return false;
+                const int x = g1_blk % kXr, b = g1_blk % kSBufs, xb = g1_itn & 1;
+                if (!bar_wait(&rfull[x], g1_blk / kXr, abort_flag, err)) return false;
+                if (g1_bc == 0 && !bar_wait(&xfull[xb], g1_itn >> 1, abort_flag, err)) return false;
+                if (!slot_wait(&sempty[b], g1_blk / kSBufs, abort_flag, err)) return false;
                 tc_fence_after();
                 const uint32_t xr = su32(xr0 + (size_t)x * kXrBytes);
                 gemm1(tS(b), tX(xb), xr, xr + kXrHalf);
                 mma_commit(&sfull[b]);
                 mma_commit(&rempty[x]);
-                if (2 * (g1_pc + 1) >= it_nch) mma_commit(&xempty[xb]);
-                ++g1_pc;
-                ++g1_pair;
+                if (kQ * (g1_bc + 1) >= g1_nch) mma_commit(&xempty[xb]);
+                ++g1_bc;
+                ++g1_blk;
                 return true;
             };
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++itn) {
+            for (int item = ibeg; item < iend && ok; item += istep, ++itn) {
                 const TcView it = src.view(item);
                 const int ab = itn % kAccBufs;
                 for (int c = 0; c < it.nch && ok; ++c, ++fill) {
-                    if (c > 0 && (c & 1) == 0) ++cur_pair;
-                    // GEMM1 runs ahead by up to kSBufs - 1 pairs: it waits only for the pair
-                    // whose epilogue comes next, and later ones go in as their inputs land
-                    while (ok && g1_pair < cur_pair + (uint32_t)kSBufs && g1_norm()) {
-                        if (g1_pair > cur_pair && !g1_ready()) break;
-                        ok = issue_gemm1();
-                    }
+                    if (c > 0 && c % kQ == 0) ++cur_blk;
+                    // the S block of this chunk has to be in before its epilogue can finish
+                    while (ok && g1_blk <= cur_blk && g1_norm()) ok = issue_gemm1();
                     if (!ok) break;
                     const int s = fill % kStages;
                     if (!bar_wait(&full[s], fill / kStages, abort_flag, err) ||
@@ -629,8 +662,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     }
                     mma_commit(&empty[s]);
                     if (c == it.nch - 1) mma_commit(&afull[ab]);
+                    // then the next block's GEMM1 as soon as its inputs are there: it runs ahead
+                    // of the epilogue, queued behind this GEMM2 rather than in front of it
+                    if (g1_blk == cur_blk + 1 && g1_norm() && g1_ready()) ok = issue_gemm1();
                 }
-                ++cur_pair;  // the next item starts a new pair
+                ++cur_blk;  // the next item starts a new block
             }
             mma_commit(fin);
             const uint64_t t0 = gtimer();
@@ -674,10 +710,10 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             if (lane == 0) bar_arrive(&xfull[xb]);
             return ok;
         };
-        uint32_t fill = 0, itn = 0, pair = 0, dlo_use = 0;
+        uint32_t fill = 0, itn = 0, blk = 0, dlo_use = 0;
         bool ok = true;
-        if (h == 0 && blockIdx.x < items) ok = put_xi(blockIdx.x, 0);
-        for (int item = blockIdx.x; item < items; item += gridDim.x, ++itn) {
+        if (h == 0 && ibeg < iend) ok = put_xi(ibeg, 0);
+        for (int item = ibeg; item < iend; item += istep, ++itn) {
             const TcView it = src.view(item);
             const int ab = itn % kAccBufs;
             const int i = it.i0 + r;
@@ -686,26 +722,26 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             const float2 s2 = make_float2((float)it.st->s, (float)it.st->s);
             // xi rows of the next item go into the other tensor-memory buffer now, so that
             // GEMM1 can run ahead across the item boundary
-            if (h == 0 && item + (int)gridDim.x < items) ok = put_xi(item + gridDim.x, itn + 1) && ok;
+            if (h == 0 && item + istep < iend) ok = put_xi(item + istep, itn + 1) && ok;
             const float uh = it.u[i], ul = it.u[it.ldv + i];  // i < ldv
             const float2 uh2 = make_float2(uh, uh), ul2 = make_float2(ul, ul);
             float dsum = 0.f;  // this thread's part of the row's ||lambda^k - lambda~^k||^2
             for (int c = 0; c < it.nch; ++c, ++fill) {
-                if (c > 0 && (c & 1) == 0) ++pair;
+                if (c > 0 && c % kQ == 0) ++blk;
                 if ((c & 1) != h) continue;  // the other group's chunk
-                const int s = fill % kStages, b = pair % kSBufs;
+                const int s = fill % kStages, b = blk % kSBufs;
                 const long long j0 = it.c0 + (long long)c * kC;
                 unsigned char *st = stage0 + (size_t)s * kStageBytes;
                 ok = ok && bar_wait(&full[s], fill / kStages, abort_flag, err);
-                ok = ok && bar_wait(&sfull[b], pair / kSBufs, abort_flag, err);
+                ok = ok && bar_wait(&sfull[b], blk / kSBufs, abort_flag, err);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
                 float v[kC];
                 tc_fence_after();
-                if (ok) tmem_ld32(tS(b) + 32u * (uint32_t)(c & 1) + lq, v);  // S, row r, this chunk's half
+                if (ok) tmem_ld32(tS(b) + 32u * (uint32_t)(c % kQ) + lq, v);  // S, row r, this chunk's columns
                 tc_fence_before();
                 __syncwarp();
-                // a pair with one chunk (odd count at the end of an item) is released for both groups
-                if (lane == 0) bar_arrive_n(&sempty[b], (c + 1 < it.nch || (c & 1)) ? 1u : 2u);
+                // the last chunk of an item also stands in for the missing chunks of its block
+                if (lane == 0) bar_arrive_n(&sempty[b], c + 1 < it.nch ? 1u : (uint32_t)(kQ - c % kQ));
                 float *P = reinterpret_cast<float *>(st + kOffP);
                 float *Qs = reinterpret_cast<float *>(st + kOffQ);
                 int dslot = 0;
@@ -809,7 +845,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                     bar_arrive(&empty[s]);
                 }
             }
-            ++pair;  // the next item starts a new pair
+            ++blk;  // the next item starts a new block
             // end of item: row partials from the GEMM2 accumulator: columns k < n of the two
             // halves give sum_j lambda_ij x_jk, column n of the first gives sum_j lambda_ij;
             // this group reads columns [16 h, 16 h + 16) of both halves
