@@ -16,7 +16,7 @@
 // block's GEMM1 (12 instructions a block), so a stage is released as soon as its epilogue is
 // done.
 //
-// CTA = 11 warps, one CTA per SM, work items of 128 rows x one column split, walked in
+// CTA = 12 warps, one CTA per SM, work items of 128 rows x a range of columns, walked in
 // chunks of 32 columns (blocks of four chunks for GEMM1):
 //   warp 0  producer: 2-D TMA loads (128-byte swizzle) of the lambda^{k-1}, lambda^{k-2}
 //           tiles (128 x 32), the chunk's transposed points with a row of ones (hi rows
@@ -29,10 +29,10 @@
 //           that take the even and the odd chunks of an item, thread = row: reads S from
 //           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
 //           consumed lambda^{k-1} tile (source of the warp's TMA store of its 32 rows of
-//           lambda^k) and the A operand of GEMM2 over the lambda^{k-2} tile, sums its
-//           32 x 32 block of the new tile by columns; the first group also copies the xi
-//           rows of the next item into tensor memory; at the end of an item both groups
-//           read the GEMM2 accumulator (row partials).
+//           lambda^k) and the A operand of GEMM2 over the lambda^{k-2} tile; the first
+//           group also copies the xi rows of the next item into tensor memory; at the end of
+//           an item both groups read the GEMM2 accumulator (row partials);
+//   warp 11 the column sums of each new tile (the column partials), off the epilogue's path.
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -57,16 +57,17 @@ constexpr int kXtBytes = 2 * kK * kC * 4;       // transposed points, hi and lo 
 // stage sit in small arrays after the point-row ring
 constexpr int kOffP = 0, kOffQ = kTiles, kOffXT = 2 * kTiles;
 constexpr int kStageBytes = 2 * kTiles + kXtBytes;
-constexpr int kYBytes = 2 * kC * 4, kColxBytes = 4 * kC * 4;
+constexpr int kYBytes = 2 * kC * 4;
 constexpr int kTxStage = kStageBytes + kYBytes;
 constexpr int kXrHalf = kQ * kC * kK * 4;       // one 128 x 32 point-row tile (16 KB)
 constexpr int kXrBytes = 2 * kXrHalf;           // hi | lo
 constexpr int kEpiWarps = 8;                    // two groups of four (one warp per lane quarter)
 constexpr int kHalf = kC / 2;                   // accumulator columns read by each group
 constexpr int kXrWarp = 2 + kEpiWarps;          // second producer
-constexpr int kThreads = (3 + kEpiWarps) * 32;
+constexpr int kColWarp = 3 + kEpiWarps;         // column sums of the new tiles
+constexpr int kThreads = (4 + kEpiWarps) * 32;  // 384 x 168 registers: the whole register file
 constexpr size_t kSmemData =
-    (size_t)kStages * kStageBytes + (size_t)kXr * kXrBytes + (size_t)kStages * (kYBytes + kColxBytes);
+    (size_t)kStages * kStageBytes + (size_t)kXr * kXrBytes + (size_t)kStages * kYBytes;
 constexpr size_t kSmem = 1024 + kSmemData + 512;
 static_assert(kStageBytes % 1024 == 0 && kXrBytes % 1024 == 0, "swizzled tiles keep 1024-byte alignment");
 static_assert(kSmem <= 232448, "shared memory budget");
@@ -471,10 +472,9 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     unsigned char *stage0 = base;
     unsigned char *xr0 = base + (size_t)kStages * kStageBytes;
     unsigned char *y0 = xr0 + (size_t)kXr * kXrBytes;
-    unsigned char *colx0 = y0 + (size_t)kStages * kYBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(colx0 + (size_t)kStages * kColxBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(y0 + (size_t)kStages * kYBytes);
     uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
-    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done + each warp's lambda^k rows stored (5 arrivals)
+    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done, each warp's lambda^k rows stored, column sums read (6 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
     uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a block in S[b]
     uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by the epilogue (4 arrivals per chunk)
@@ -486,9 +486,8 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     uint64_t *aempty = afull + kAccBufs;    // [kAccBufs] accumulator read (one per warp)
     uint64_t *dloe = aempty + kAccBufs;     // [2 kDloBufs] delta form: the GEMM2 that read a DLO slot done
     uint64_t *fin = dloe + 2 * kDloBufs;    // all MMAs done (teardown)
-    int *ticket = reinterpret_cast<int *>(fin + 1);  // [kStages]
-    volatile int *abort_flag = ticket + kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ticket + kStages + 1);
+    volatile int *abort_flag = reinterpret_cast<int *>(fin + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ibeg = src.begin(), iend = src.end(), istep = src.step();  // this CTA's items
@@ -496,9 +495,8 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             bar_init(&full[s], 1);
-            bar_init(&empty[s], 5);
+            bar_init(&empty[s], 6);
             bar_init(&lamr[s], 4);
-            ticket[s] = 0;
         }
         for (int b = 0; b < kSBufs; ++b) {
             bar_init(&sfull[b], 1);
@@ -673,6 +671,68 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             while (!bar_try(fin, 0) && gtimer() - t0 < 500000000ull) {
             }
         }
+    } else if (warp == kColWarp) {
+        // ---------------------------------------------------------------- column sums
+        // once the epilogue has written a chunk's tiles: the sums over the block's rows of each
+        // column of the new tile (lambda^k, or its change in delta form; rows past the last
+        // count as zero), in a fixed order: per lane quarter q, lane = (row group rg of 8 rows,
+        // column group g of 4 columns) sums its 8 rows, a butterfly adds the four row groups,
+        // and the quarters are added in order
+        uint32_t fill = 0;
+        bool ok = true;
+        const int g = lane & 7, rg = lane >> 3;
+        for (int item = ibeg; item < iend && ok; item += istep) {
+            const TcView it = src.view(item);
+            const int vrows = min(kM, it.row_end - it.i0);  // rows of the block that exist
+            for (int c = 0; c < it.nch; ++c, ++fill) {
+                const int s = fill % kStages;
+                ok = __all_sync(0xffffffffu, bar_wait(&lamr[s], fill / kStages, abort_flag, err));
+                if (!ok) break;
+                const float *Red = reinterpret_cast<const float *>(stage0 + (size_t)s * kStageBytes +
+                                                                   (it.delta ? kOffQ : kOffP));
+                // the four quarters side by side (independent chains), each in row order
+                float2 ca[4], cb[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ca[q] = cb[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int rr = 32 * q + 8 * rg + t;
+                        const float4 x = rr < vrows ? *reinterpret_cast<const float4 *>(Red + rr * 32 + ((g ^ (rr & 7)) << 2))
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                        ca[q] = __fadd2_rn(ca[q], make_float2(x.x, x.y));
+                        cb[q] = __fadd2_rn(cb[q], make_float2(x.z, x.w));
+                    }
+                }
+#pragma unroll
+                for (int o = 8; o <= 16; o <<= 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 oa = make_float2(__shfl_xor_sync(0xffffffffu, ca[q].x, o), __shfl_xor_sync(0xffffffffu, ca[q].y, o));
+                        const float2 ob = make_float2(__shfl_xor_sync(0xffffffffu, cb[q].x, o), __shfl_xor_sync(0xffffffffu, cb[q].y, o));
+                        ca[q] = __fadd2_rn(ca[q], oa);
+                        cb[q] = __fadd2_rn(cb[q], ob);
+                    }
+                }
+                const float2 ta = __fadd2_rn(__fadd2_rn(__fadd2_rn(ca[0], ca[1]), ca[2]), ca[3]);
+                const float2 tb = __fadd2_rn(__fadd2_rn(__fadd2_rn(cb[0], cb[1]), cb[2]), cb[3]);
+                if (rg == 0 && !*abort_flag) {
+                    const long long j = it.c0 + (long long)c * kC + 4 * g;
+                    float *dst = it.colpart + (long long)it.rb * it.ld + j;
+                    const float cv[4] = {ta.x, ta.y, tb.x, tb.y};
+                    if (j + 4 <= it.c1) {
+                        *reinterpret_cast<float4 *>(dst) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (j + e < it.c1) dst[e] = cv[e];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(&empty[s]);
+            }
+        }
     } else {
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
@@ -753,8 +813,11 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 }
                 if (ok) {
                     const float *Y = reinterpret_cast<const float *>(y0 + (size_t)s * kYBytes);
-                    const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N) ||
-                                      (it.i0 + kM > it.row_end);
+                    // the checks of the diagonal and of padding columns; rows past the last
+                    // (a partial last block) need none: their values are neither stored (the
+                    // maps clip them), nor summed by columns (warp 11 masks them), nor kept in
+                    // the row partials
+                    const bool edge = (j0 < (long long)it.i0 + kM && j0 + kC > it.i0) || (j0 + kC > it.N);
                     // each half of the row at a time; in delta form the half's low parts go to
                     // this warp's lane quarter of the group's DLO slot right away
 #define CR_EPI(E, A, D)                                                                                \
@@ -788,59 +851,10 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    // this warp's 32 rows of lambda^k go out at once (rows >= N are clipped)
+                    // this warp's 32 rows of lambda^k go out at once (rows past the last are clipped)
                     if (ok && it.i0 + 32 * q < it.row_end)
                         tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q - it.row0);
                     bar_arrive(&lamr[s]);
-                }
-                // what the C^T reductions see: lambda^k (P), or its change (Qs) in delta form
-                const float *Red = it.delta ? Qs : P;
-                if (ok) {
-                    // column sums of this warp's 32 x 32 block, read back from the new tile:
-                    // lane = (row group rg of 8 rows, column group g of 4 columns), then a
-                    // butterfly over the 4 row groups (every lane ends with the same sums)
-                    const int g = lane & 7, rg = lane >> 3;
-                    float2 ca = make_float2(0.f, 0.f), cb = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int rr = 32 * q + 8 * rg + t;
-                        const float4 x = *reinterpret_cast<const float4 *>(Red + rr * 32 + ((g ^ (rr & 7)) << 2));
-                        ca = __fadd2_rn(ca, make_float2(x.x, x.y));
-                        cb = __fadd2_rn(cb, make_float2(x.z, x.w));
-                    }
-#pragma unroll
-                    for (int o = 8; o <= 16; o <<= 1) {
-                        const float2 oa = make_float2(__shfl_xor_sync(0xffffffffu, ca.x, o),
-                                                      __shfl_xor_sync(0xffffffffu, ca.y, o));
-                        const float2 ob = make_float2(__shfl_xor_sync(0xffffffffu, cb.x, o),
-                                                      __shfl_xor_sync(0xffffffffu, cb.y, o));
-                        ca = __fadd2_rn(ca, oa);
-                        cb = __fadd2_rn(cb, ob);
-                    }
-                    float *colx = reinterpret_cast<float *>(colx0 + (size_t)s * kColxBytes);
-                    if (rg == 0) *reinterpret_cast<float4 *>(colx + q * kC + 4 * g) = make_float4(ca.x, ca.y, cb.x, cb.y);
-                }
-                __syncwarp();
-                // last warp through: column partials in quarter order
-                int last = 0;
-                if (lane == 0) {
-                    __threadfence_block();
-                    last = (atomicAdd(&ticket[s], 1) == 3);
-                }
-                last = __shfl_sync(0xffffffffu, last, 0);
-                __syncwarp();
-                if (last) {
-                    __threadfence_block();
-                    if (ok && !*abort_flag) {
-                        const float *colx = reinterpret_cast<const float *>(colx0 + (size_t)s * kColxBytes);
-                        const float cv = ((colx[lane] + colx[kC + lane]) + colx[2 * kC + lane]) + colx[3 * kC + lane];
-                        const long long j = j0 + lane;
-                        if (j < it.c1) it.colpart[(long long)it.rb * it.ld + j] = cv;
-                    }
-                    __syncwarp();
-                    if (lane == 0) ticket[s] = 0;
-                }
-                if (lane == 0) {
                     tma_store_wait_read();  // the stage may be refilled once the store has read it
                     bar_arrive(&empty[s]);
                 }
