@@ -705,6 +705,10 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                         cb[q] = __fadd2_rn(cb[q], make_float2(x.z, x.w));
                     }
                 }
+                // the tile has been read (the arrive orders this warp's loads before it): the
+                // stage may be refilled while the sums are finished
+                __syncwarp();
+                if (lane == 0) bar_arrive(&empty[s]);
 #pragma unroll
                 for (int o = 8; o <= 16; o <<= 1) {
 #pragma unroll
@@ -729,8 +733,6 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                             if (j + e < it.c1) dst[e] = cv[e];
                     }
                 }
-                __syncwarp();
-                if (lane == 0) bar_arrive(&empty[s]);
             }
         }
     } else {
