@@ -150,7 +150,6 @@ cr_status enqueue_sweep(cr_ctx *c, long long k, cudaEvent_t e0) {
         a.colpart = (float *)c->colpart;
         a.err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->st) + offsetof(DevState, err));
         a.lmaps = c->tc_ld;
-        a.smaps = c->tc_st;
         a.p_host = P;
         a.adaptive = c->adaptive ? 1 : 0;
         a.dpart = (float *)c->dpart;
@@ -465,19 +464,15 @@ cr_status create_impl(cr_ctx *c, const double *X, const double *ybar) {
         CR_TRY(dev_alloc(c, &c->xi_rm, 2 * rm));
         CR_CUDA(cudaMemsetAsync(c->xi_rm, 0, 2 * rm * sizeof(float), c->stream));
         CR_CUDA(launch_tc_points(c->X, N, n, c->ldv, c->xr, c->xt, c->stream));
-        CUtensorMap hl[3], hs[3];
+        // one map per buffer, box 32 x 128: the loads of lambda^{k-1}, lambda^{k-2} and the store
+        // of lambda^k (rows past the buffer's last are filled with zeros / not written)
+        CUtensorMap hl[3];
         memset(hl, 0, sizeof(hl));
-        memset(hs, 0, sizeof(hs));
-        for (int i = 0; i < nbuf; ++i) {
+        for (int i = 0; i < nbuf; ++i)
             CR_CUDA(make_tmap_2d(&hl[i], (const float *)c->lam[i], c->ld, LR, c->ld, 32, 128, true));
-            CR_CUDA(make_tmap_2d(&hs[i], (const float *)c->lam[i], c->ld, LR, c->ld, 32, 32, true));
-        }
         CR_TRY(dev_alloc(c, &c->tc_ld, 3));
-        CR_TRY(dev_alloc(c, &c->tc_st, 3));
         memcpy(c->tc_lam_ld, hl, sizeof(hl));
-        memcpy(c->tc_lam_st, hs, sizeof(hs));
         CR_CUDA(cudaMemcpyAsync(c->tc_ld, c->tc_lam_ld, sizeof(hl), cudaMemcpyHostToDevice, c->stream));
-        CR_CUDA(cudaMemcpyAsync(c->tc_st, c->tc_lam_st, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
         CR_CUDA(make_tmap_2d(&c->tcm.XRh, c->xr, 32, c->ldv, 32, 32, 128, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XRl, c->xr + rm, 32, c->ldv, 32, 32, 128, true));
         CR_CUDA(make_tmap_2d(&c->tcm.XT, c->xt, c->ldv, 64, c->ldv, 32, 64, true));

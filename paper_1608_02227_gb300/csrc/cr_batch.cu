@@ -147,10 +147,7 @@ void fill_desc(const cr_batch *b, const cr_ctx *c, InstDesc *d, int id) {
     d->rf_c = c->rf_c;
     d->dgroups = c->S * (c->tc ? 2 : 1);  // the tensor-core sweep keeps two groups per split
     if (c->tc) {
-        for (int i = 0; i < 3; ++i) {
-            d->tc_lam_ld[i] = c->tc_lam_ld[i];
-            d->tc_lam_st[i] = c->tc_lam_st[i];
-        }
+        for (int i = 0; i < 3; ++i) d->tc_lam_ld[i] = c->tc_lam_ld[i];
         d->tc_xrh = c->tcm.XRh;
         d->tc_xrl = c->tcm.XRl;
         d->tc_xt = c->tcm.XT;

@@ -65,8 +65,8 @@ struct cr_ctx {
     CUtensorMap *tm_ld = nullptr;  // adaptive step: device copy of tm_lam (roles chosen on the device)
     TmaMaps tm{};
     bool tc = false;             // CR_MIXED_TF32: tensor-core sweep (cr_sweep_tc.cu)
-    CUtensorMap *tc_ld = nullptr, *tc_st = nullptr;  // device arrays: load / store maps of the buffers
-    CUtensorMap tc_lam_ld[3], tc_lam_st[3];          // host copies of the same maps (batch descriptors)
+    CUtensorMap *tc_ld = nullptr;                    // device array: maps of the buffers (box 32 x 128)
+    CUtensorMap tc_lam_ld[3];                        // host copies of the same maps (batch descriptors)
     TcMaps tcm{};
     float *xr = nullptr, *xt = nullptr, *xi_rm = nullptr;
     // graph of graph_iters iterations starting at an even k

@@ -190,8 +190,7 @@ struct TcSweepArgs {
     float *rowpart;          // S x N x (NP+1)
     float *colpart;          // RB x ld (128-row blocks)
     int *err;
-    const CUtensorMap *lmaps;  // device array: load maps of the multiplier buffers (box 32 x 128)
-    const CUtensorMap *smaps;  // device array: store maps of the same buffers (box 32 x 32)
+    const CUtensorMap *lmaps;  // device array: maps of the multiplier buffers (box 32 x 128; loads and stores)
     int p_host;              // constant step: buffer holding lambda^{k-1}
     int adaptive;
     int delta;               // 1: the reductions are of lambda^k - lambda^{k-1}
@@ -221,9 +220,9 @@ struct WorkItem {
 struct InstDesc {
     CUtensorMap tm_lam[3];               // lam[0..2]: [N][ld], box 128 x R (the third with the adaptive step)
     CUtensorMap tm_x, tm_y, tm_xi, tm_u; // as in TmaMaps
-    // tensor-core instances (tc = 1): load (box 32 x 128) and store (box 32 x 32) maps of the
-    // multiplier buffers and the point / y maps of TcMaps
-    CUtensorMap tc_lam_ld[3], tc_lam_st[3];
+    // tensor-core instances (tc = 1): maps of the multiplier buffers (box 32 x 128, loads and the
+    // store) and the point / y maps of TcMaps
+    CUtensorMap tc_lam_ld[3];
     CUtensorMap tc_xrh, tc_xrl, tc_xt, tc_y;
     int tc;
     int delta;                           // reductions of lambda^k - lambda^{k-1} (see cr_refresh.cu)

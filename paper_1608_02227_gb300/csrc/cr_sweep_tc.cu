@@ -28,11 +28,12 @@
 //   warps 2-9  epilogue in two groups of four (one warp per tensor-memory lane quarter)
 //           that take the even and the odd chunks of an item, thread = row: reads S from
 //           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
-//           consumed lambda^{k-1} tile (source of the warp's TMA store of its 32 rows of
-//           lambda^k) and the A operand of GEMM2 over the lambda^{k-2} tile; the first
+//           consumed lambda^{k-1} tile (the source of the TMA store) and the A operand of
+//           GEMM2 over the lambda^{k-2} tile; the first
 //           group also copies the xi rows of the next item into tensor memory; at the end of
 //           an item both groups read the GEMM2 accumulator (row partials);
-//   warp 11 the column sums of each new tile (the column partials), off the epilogue's path.
+//   warp 11 the TMA store of each new lambda^k tile (128 rows) and its column sums (the
+//           column partials), off the epilogue's path.
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -279,7 +280,7 @@ __device__ __forceinline__ float tf32_lo(float v) { return v - __uint_as_float(_
 // Everything one work item of 128 rows x one column split needs: the tensor maps of its
 // instance, its vectors and partial buffers, the roles of its multiplier buffers and its bounds.
 struct TcView {
-    const CUtensorMap *P, *Q, *Qs;           // lambda^{k-1}, lambda^{k-2} loads; store map of lambda^k
+    const CUtensorMap *P, *Q, *R;            // lambda^{k-1}, lambda^{k-2} (loads), lambda^k (store)
     const CUtensorMap *XRh, *XRl, *XT, *Y;   // point rows (hi, lo), transposed points, y (hi, lo)
     const float *xi_rm, *u;
     float *rowpart, *colpart, *dpart;
@@ -319,7 +320,7 @@ struct TcSrcSingle {
         lam_roles(a->st, a->adaptive, a->p_host, &bp, &bq, &br);
         v.P = a->lmaps + bp;
         v.Q = a->lmaps + bq;
-        v.Qs = a->smaps + br;
+        v.R = a->lmaps + br;
         v.delta = a->delta;
         v.XRh = XRh, v.XRl = XRl, v.XT = XT, v.Y = Y;
         v.xi_rm = a->xi_rm;
@@ -376,7 +377,7 @@ struct TcSrcBatch {
         lam_roles(D.st, D.adaptive, (int)(D.st->k & 1), &bp, &bq, &br);
         v.P = &D.tc_lam_ld[bp];
         v.Q = &D.tc_lam_ld[bq];
-        v.Qs = &D.tc_lam_st[br];
+        v.R = &D.tc_lam_ld[br];
         v.delta = D.delta;
         v.XRh = &D.tc_xrh, v.XRl = &D.tc_xrl, v.XT = &D.tc_xt, v.Y = &D.tc_y;
         v.xi_rm = D.xi_rm;
@@ -474,7 +475,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     unsigned char *y0 = xr0 + (size_t)kXr * kXrBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(y0 + (size_t)kStages * kYBytes);
     uint64_t *full = bars;                  // [kStages] TMA data of a stage landed
-    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done, each warp's lambda^k rows stored, column sums read (6 arrivals)
+    uint64_t *empty = full + kStages;       // [kStages] GEMM2 done; lambda^k stored and read for the column sums (2 arrivals)
     uint64_t *lamr = empty + kStages;       // [kStages] lambda tiles written by the epilogue (4 arrivals)
     uint64_t *sfull = lamr + kStages;       // [kSBufs] GEMM1 result of a block in S[b]
     uint64_t *sempty = sfull + kSBufs;      // [kSBufs] S[b] read by the epilogue (4 arrivals per chunk)
@@ -495,7 +496,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             bar_init(&full[s], 1);
-            bar_init(&empty[s], 6);
+            bar_init(&empty[s], 2);
             bar_init(&lamr[s], 4);
         }
         for (int b = 0; b < kSBufs; ++b) {
@@ -688,8 +689,10 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 const int s = fill % kStages;
                 ok = __all_sync(0xffffffffu, bar_wait(&lamr[s], fill / kStages, abort_flag, err));
                 if (!ok) break;
-                const float *Red = reinterpret_cast<const float *>(stage0 + (size_t)s * kStageBytes +
-                                                                   (it.delta ? kOffQ : kOffP));
+                const unsigned char *st = stage0 + (size_t)s * kStageBytes;
+                // lambda^k of the 128 rows goes out at once (rows past the buffer's last are clipped)
+                if (lane == 0) tma_store(it.R, st + kOffP, (int)(it.c0 + (long long)c * kC), it.i0 - it.row0);
+                const float *Red = reinterpret_cast<const float *>(st + (it.delta ? kOffQ : kOffP));
                 // the four quarters side by side (independent chains), each in row order
                 float2 ca[4], cb[4];
 #pragma unroll
@@ -705,10 +708,14 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                         cb[q] = __fadd2_rn(cb[q], make_float2(x.z, x.w));
                     }
                 }
-                // the tile has been read (the arrive orders this warp's loads before it): the
-                // stage may be refilled while the sums are finished
+                // the tile has been read (the arrive orders this warp's loads before it) and so,
+                // once waited for, has the store: the stage may be refilled while the sums are
+                // finished
                 __syncwarp();
-                if (lane == 0) bar_arrive(&empty[s]);
+                if (lane == 0) {
+                    tma_store_wait_read();
+                    bar_arrive(&empty[s]);
+                }
 #pragma unroll
                 for (int o = 8; o <= 16; o <<= 1) {
 #pragma unroll
@@ -735,6 +742,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 }
             }
         }
+        if (lane == 0) tma_store_wait_all();
     } else {
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
@@ -852,14 +860,7 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    // this warp's 32 rows of lambda^k go out at once (rows past the last are clipped)
-                    if (ok && it.i0 + 32 * q < it.row_end)
-                        tma_store(it.Qs, P + 32 * 32 * q, (int)j0, it.i0 + 32 * q - it.row0);
-                    bar_arrive(&lamr[s]);
-                    tma_store_wait_read();  // the stage may be refilled once the store has read it
-                    bar_arrive(&empty[s]);
-                }
+                if (lane == 0) bar_arrive(&lamr[s]);  // the store and the column sums are warp 11's
             }
             ++blk;  // the next item starts a new block
             // end of item: row partials from the GEMM2 accumulator: columns k < n of the two
@@ -887,7 +888,6 @@ __device__ __forceinline__ void sweep_tc_body(const Src &src, int *err) {
             }
             ok = ok && ok2;
         }
-        tma_store_wait_all();
     }
     tc_fence_before();
     __syncthreads();
