@@ -86,7 +86,9 @@ typedef struct cr_options {
     int accelerate;      /* 1: P-APG momentum (Step 4); 0: projected dual gradient ascent */
     int check_every;     /* iterations between convergence checks in cr_solve (>= 1) */
     int graph_iters;     /* iterations per captured CUDA graph in cr_dual_step (even; 0: no graphs) */
-    int tile_cols;       /* columns of Lambda per work item (multiple of 128; 0: chosen by the library) */
+    int tile_cols;       /* columns of Lambda per work item (multiple of 128; 0: chosen by the library;
+                            with 0 the tensor-core sweep gives every CTA an equal range of
+                            32-column chunks instead of whole items) */
     int deterministic;   /* kept for ABI stability: every reduction is already in a fixed order */
     int step_rule;       /* cr_step_rule: CR_STEP_CONSTANT (1/L, Figure "papg") or CR_STEP_ADAPTIVE */
     double upsilon;      /* CR_STEP_ADAPTIVE: the factor upsilon > 1 of the step rule (default 2) */
