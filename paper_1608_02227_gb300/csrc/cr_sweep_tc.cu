@@ -13,8 +13,7 @@
 // this kernel: the tensor pipe is paid per instruction, one K step of 8), so GEMM1 covers a
 // block of four 32-column chunks with each instruction (N = 128) and GEMM2 the two halves of
 // the operand split.  GEMM2 (8 instructions a chunk) goes to the tensor pipe before the next
-// block's GEMM1 (12 instructions a block), so a stage is released as soon as its epilogue is
-// done.
+// block's GEMM1 (12 instructions a block), so a stage is released soon after its epilogue.
 //
 // CTA = 12 warps, one CTA per SM, work items of 128 rows x a range of columns, walked in
 // chunks of 32 columns (blocks of four chunks for GEMM1):
@@ -29,11 +28,13 @@
 //           that take the even and the odd chunks of an item, thread = row: reads S from
 //           tensor memory, forms lambda^k (packed FP32x2 arithmetic), writes it over the
 //           consumed lambda^{k-1} tile (the source of the TMA store) and the A operand of
-//           GEMM2 over the lambda^{k-2} tile; the first
-//           group also copies the xi rows of the next item into tensor memory; at the end of
-//           an item both groups read the GEMM2 accumulator (row partials);
+//           GEMM2 over the lambda^{k-2} tile (in delta form the change, its TF32 low part
+//           going to the group's slot in tensor memory); the first group also copies the xi
+//           rows of the next item into tensor memory; at the end of an item both groups read
+//           the GEMM2 accumulator (row partials);
 //   warp 11 the TMA store of each new lambda^k tile (128 rows) and its column sums (the
-//           column partials), off the epilogue's path.
+//           column partials), off the epilogue's path; it releases the stage once it has read
+//           the tile and the store has read it too.
 // Every wait is bounded (2 s); on expiry the CTA aborts cleanly and reports CR_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
